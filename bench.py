@@ -1,0 +1,292 @@
+"""Throughput bench of the BSDE solver (path-steps/s at d = 10).
+
+One step = one full solve of the American basket put d = 10 (n = 4000 points,
+M = 4000 paths, N = 100 Euler steps, total degree 3 -> p = 364 basis
+functions, K_it = 12 Picard iterations): every row of the hot path (points,
+basis matrix, path simulation + evaluation + reduction, Gram + RHS, Cholesky
++ refinement, update, price/delta read-out) runs once per iteration.
+Metric: path-steps/s = K_it n M N / time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own independent problem (its
+own seed): weak scaling with no data-path collective.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "path-steps/s incl. u^k,∇u^k,Lu^k eval at d=10 (vs FP64 plain); p50/p99 solve ms"
+UNIT = "path-steps/s"
+CONFIG = "c4"
+
+# FP32 arithmetic of one path-step of the d = 10 kernel, counted from the
+# source (an FMA counts 2): correlation L Z 100, local volatility 10 x 8,
+# drift and update 10 x 7, Box-Muller 5 pairs x 10 -> 300.  The per-path
+# evaluation of u^k and its derivatives (~11k flops for p = 364) adds
+# ~110 per step at N = 100; only the 300 of the Euler step are counted.
+FLOPS_PER_PATH_STEP = 300.0
+SMS, FP32_LANES = 152, 128
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(cfg, budget_s=12.0):
+    """The oracle (FP64, C, threads over points) on this host's cores: one
+    iteration's corrections at a bounded sample of points; path-steps/s."""
+    import numpy as np
+    from oracle import bsde_oracle as O
+    nth = os.cpu_count() or 1
+    nu = O.multi_index_set(cfg["d"] + 1, cfg["eta"], cfg.get("q", 1.0))
+    alpha = np.zeros(len(nu)); alpha[0] = 5.0
+    t, x = O.points(cfg, 0)
+    # calibrate on one point, then size the sample to the budget
+    t0 = time.perf_counter()
+    O.correction(cfg, nu, alpha, 0, np.arange(1), t[:1], x[:, :1], nthreads=1)
+    per_point = max(1e-6, time.perf_counter() - t0)
+    npts = max(nth, int(budget_s * nth / per_point) // nth * nth)
+    npts = min(npts, cfg["n"])
+    idx = np.arange(npts)
+    t0 = time.perf_counter()
+    O.correction(cfg, nu, alpha, 0, idx, t[idx], x[:, idx], nthreads=nth)
+    el = time.perf_counter() - t0
+    steps = npts * cfg["M"] * cfg["N"]
+    return {"value": steps / el, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": "one Picard iteration, corrections c_i at %d of the %d points (M=%d paths, N=%d "
+                      "steps each, p=%d), FP64 C oracle, %.1f s" % (npts, cfg["n"], cfg["M"], cfg["N"],
+                                                                    len(nu), el)}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    cfg = workloads.config(CONFIG)
+    # each step: a bounded sample of the same workload (one iteration at a
+    # subset of points), sized so that warmup + steps take a few minutes
+    for _ in range(max(0, min(args.warmup, 1))):
+        cpu_oracle_rate(cfg, budget_s=2.0)
+    vals = []
+    last = None
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        last = cpu_oracle_rate(cfg, budget_s=max(2.0, min(20.0, 120.0 / max(1, args.steps))))
+        vals.append(last["value"])
+    el = time.perf_counter() - t_all
+    v = sum(vals) / len(vals)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": cfg["name"], "d": 10, "n": cfg["n"], "M": cfg["M"], "N": cfg["N"],
+                       "eta": 3, "p": 364, "K_it": cfg["K_it"], "sample": last["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1102_4666_gb300 as G
+
+    cfg = workloads.config(CONFIG)
+    cfg["seed"] = cfg["seed"] + 1000 * rank  # independent problem per rank
+    stream = torch.cuda.Stream(device=dev)
+    s = G.Solver(cfg, precision="mixed", device=local, stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step(timing=1):
+        return s.solve(use_graph=1, timing=timing)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    reps = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between steps (on the solve's stream)
+            reps.append(step())
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    steps_per_solve = workloads.path_steps(cfg)
+    value = world * args.steps * steps_per_solve / (ms * 1e-3)
+    launches = sum(r.kernel_launches for r in reps)
+    path_ms = sum(r.ms_paths for r in reps) / sum(r.path_launches for r in reps)
+
+    # end to end through the public API with host buffers: model, grid and
+    # parameters copied from host, report (price, delta, residuals) to host
+    e2e_ms = None
+    h2d = d2h = 0
+    if rank == 0 or True:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.set_model(cfg)
+            s.set_grid(cfg)
+            r = s.solve(use_graph=1, timing=0)
+            _ = (r.price, list(r.delta))
+        e2e_s = time.perf_counter() - t0
+        e2e_ms = e2e_s * 1e3 / args.steps
+        p = 364
+        h2d = p * 8 + p + cfg["d"] * 8 + 8 + 4   # basis tables, log S0, key, status reset
+        d2h = (1 + 16 + 3 * 64) * 8 + 4          # report block and status word
+    e2e_val = world * steps_per_solve / (e2e_ms * 1e-3)
+
+    # plain FP64 comparator: the same kernels in FP64, one request, no graph
+    fp64 = None
+    if rank == 0 and not args.no_fp64:
+        cfg64 = dict(cfg)
+        cfg64["K_it"] = 1
+        s64 = G.Solver(cfg64, precision="fp64", device=local)
+        s64.solve(use_graph=0, K_it=1)
+        r64 = s64.solve(use_graph=0, K_it=1, timing=1)
+        s64.close()
+        fp64 = {"value": r64.path_steps_per_s, "unit": UNIT,
+                "sample": "one iteration of the same workload in FP64, direct launches",
+                "path_kernel_ms": r64.ms_paths}
+
+    s.close()
+    if rank != 0:
+        return 0
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    launch_steps = cfg["n"] * cfg["M"] * cfg["N"]
+    achieved = FLOPS_PER_PATH_STEP * launch_steps / (path_ms * 1e-3) / 1e12
+    cpu = cpu_oracle_rate(cfg, budget_s=args.cpu_budget) if not args.no_cpu else None
+    rep0 = reps[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 paths / f64 sums / 3xtf32 gram / f64 solve",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "d": 10, "n": cfg["n"], "M": cfg["M"], "N": cfg["N"],
+                   "eta": 3, "p": rep0.p, "K_it": cfg["K_it"], "precision": "mixed",
+                   "l2": "flushed between steps (256 MB write)", "graph": True},
+        "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,float,10>", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock %.0f MHz" % sm_mhz,
+                     "flops_per_path_step": FLOPS_PER_PATH_STEP, "path_kernel_ms": path_ms},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                   "reasons": clk.get("reasons")},
+        "fp64_plain": fp64,
+        "solve": {"price": rep0.price, "delta0": rep0.delta[0], "ms_paths": rep0.ms_paths,
+                  "ms_gram": rep0.ms_gram, "ms_solve": rep0.ms_solve, "ms_total": rep0.ms_total},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

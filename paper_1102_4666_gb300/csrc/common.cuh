@@ -1,0 +1,179 @@
+// common.cuh -- shared device helpers and the internal launch interfaces of
+// the BSDE kernels (Labart & Lelong, Algorithm 2).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#define BSDE_DMAX 16
+#define BSDE_NNZ_MAX 8  // active variates per basis function
+
+// Philox4x32-10 counter tags (top byte of the fourth counter word)
+#define TAG_PTS 1u
+#define TAG_U 2u
+#define TAG_Z 3u
+#define TAG_B 4u
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
+// multiplies words 0 and 2 by the Philox constants, swaps and xors the high
+// halves with words 1/3 and the round key.  Key schedule: Weyl increments.
+// ---------------------------------------------------------------------------
+struct Philox {
+  uint32_t k0, k1;
+  __device__ __forceinline__ uint4 operator()(uint32_t c0, uint32_t c1, uint32_t c2,
+                                              uint32_t c3) const {
+    uint32_t a = k0, b = k1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+      const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+      const uint32_t n0 = hi1 ^ c1 ^ a;
+      const uint32_t n2 = hi0 ^ c3 ^ b;
+      c0 = n0;
+      c1 = lo1;
+      c2 = n2;
+      c3 = lo0;
+      a += 0x9E3779B9u;
+      b += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Precision traits: the FP32 path uses the fast hardware approximations
+// (MUFU) where their error is far below the Monte Carlo noise; the FP64 path
+// uses CUDA's double-precision math library.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Math;
+
+template <>
+struct Math<float> {
+  // Box-Muller pair from two 32-bit words: u = (w + 1/2) 2^-32 in (0,1]
+  __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, float& z0,
+                                                    float& z1) {
+    const float u0 = fmaf(__uint2float_rn(w0), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float u1 = fmaf(__uint2float_rn(w1), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float rad = sqrtf(fmaxf(-2.0f * __logf(u0), 0.0f));
+    float s, c;
+    // angle 2 pi u1 - pi keeps the argument in (-pi, pi]; cos/sin flip sign
+    __sincosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f), &s, &c);
+    z0 = -rad * c;
+    z1 = -rad * s;
+  }
+  __device__ __forceinline__ static float exp(float x) { return __expf(x); }
+  __device__ __forceinline__ static float tanh(float x) {
+    // 1 - 2 / (e^{2x} + 1): exact limits +-1, absolute error ~1e-7
+    return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f);
+  }
+  __device__ __forceinline__ static float sqrt(float x) { return sqrtf(x); }
+  __device__ __forceinline__ static float fabs(float x) { return fabsf(x); }
+  __device__ __forceinline__ static float fmax(float a, float b) { return fmaxf(a, b); }
+};
+
+template <>
+struct Math<double> {
+  __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, double& z0,
+                                                    double& z1) {
+    const double u0 = ((double)w0 + 0.5) * 2.3283064365386962890625e-10;
+    const double u1 = ((double)w1 + 0.5) * 2.3283064365386962890625e-10;
+    const double rad = ::sqrt(-2.0 * ::log(u0));
+    double s, c;
+    sincospi(2.0 * u1, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+  }
+  __device__ __forceinline__ static double exp(double x) { return ::exp(x); }
+  __device__ __forceinline__ static double tanh(double x) { return ::tanh(x); }
+  __device__ __forceinline__ static double sqrt(double x) { return ::sqrt(x); }
+  __device__ __forceinline__ static double fabs(double x) { return ::fabs(x); }
+  __device__ __forceinline__ static double fmax(double a, double b) { return ::fmax(a, b); }
+};
+
+// ---------------------------------------------------------------------------
+// Host-side description of one solve, shared by the launchers.
+// ---------------------------------------------------------------------------
+struct ModelHost {
+  int d = 0;
+  int vol_kind = 0;
+  int payoff = 0;
+  int obstacle = 0;
+  double T = 1.0, r = 0.0, lambda = 0.0, K = 0.0;
+  double a[BSDE_DMAX] = {0}, kappa[BSDE_DMAX] = {0}, div[BSDE_DMAX] = {0};
+  double w[BSDE_DMAX] = {0}, S0[BSDE_DMAX] = {0};
+  double b = 0.0, s_dupire = 0.0;
+  double C[BSDE_DMAX * BSDE_DMAX] = {0};
+  double L[BSDE_DMAX * BSDE_DMAX] = {0};
+};
+
+struct GridHost {
+  int n = 0;
+  int resample = 1;
+  double lo[BSDE_DMAX + 1] = {0}, hi[BSDE_DMAX + 1] = {0};
+};
+
+// Device pointers of one resident problem (one context or one served request)
+struct ProblemDev {
+  int n = 0, n_pad = 0, p = 0, p_pad = 0, eta = 0, chunks = 0;
+  double* t = nullptr;        // [n]
+  double* x = nullptr;        // [d][n]
+  double* B = nullptr;        // [p][n_pad] FP64 basis matrix, point index fastest
+  float* Bhi = nullptr;       // [p_pad][n_pad] tf32-rounded high part (mixed)
+  float* Blo = nullptr;       // [p_pad][n_pad] tf32-rounded remainder (mixed)
+  double* partial = nullptr;  // [n][chunks] per-chunk sums of a_m
+  double* c = nullptr;        // [n] corrections
+  double* A = nullptr;        // [p][p] Gram matrix, then its Cholesky factor
+  float* gram_part = nullptr; // split-K partial tiles of the tensor-core Gram
+  double* rhs = nullptr;      // [p]
+  double* delta = nullptr;    // [p] solution of the normal equations
+  double* res = nullptr;      // [p] refinement residual
+  double* v = nullptr;        // [n] B delta
+  double* alpha = nullptr;    // [p] coefficients (FP64 master)
+  float* alpha32 = nullptr;   // [p] FP32 copy for the mixed path kernel
+  uint2* pairs = nullptr;     // [p] packed (variate, degree) bytes
+  uint8_t* nnz = nullptr;     // [p] active variates per basis function
+  uint32_t* key = nullptr;    // [2] Philox key
+  int* status = nullptr;      // [1] device status bits
+  double* out = nullptr;      // report block (see OUT_* offsets)
+};
+
+// offsets in ProblemDev::out
+#define OUT_PRICE 0
+#define OUT_DUDX 1                        // d values
+#define OUT_PRICE_IT (1 + BSDE_DMAX)      // BSDE_MAX_IT values
+#define OUT_RES2 (OUT_PRICE_IT + 64)
+#define OUT_RESI (OUT_RES2 + 64)
+#define OUT_SIZE (OUT_RESI + 64)
+
+// device status bits
+#define ST_NOT_PD 1
+#define ST_TIMEOUT 2
+#define ST_BADARG 4
+
+// launchers (one translation unit each)
+void launch_points(const ModelHost& m, const GridHost& g, const ProblemDev& P, uint32_t k,
+                   cudaStream_t st);
+void launch_basis(const ModelHost& m, const GridHost& g, const ProblemDev& P, bool mixed,
+                  cudaStream_t st);
+// path kernel: returns cudaSuccess or the launch error
+cudaError_t launch_paths(const ModelHost& m, const GridHost& g, const ProblemDev& P, int M, int N,
+                         uint32_t k, bool mixed, int tpb, int ppt, cudaStream_t st);
+void launch_reduce_c(const ProblemDev& P, int M, cudaStream_t st);
+void launch_gram_f64(const ProblemDev& P, cudaStream_t st);
+cudaError_t launch_gram_tc(const ProblemDev& P, cudaStream_t st);
+int gram_tc_splits(const ProblemDev& P);
+void launch_rhs(const ProblemDev& P, cudaStream_t st);
+void launch_cholesky(const ProblemDev& P, cudaStream_t st);
+void launch_chol_solve(const ProblemDev& P, const double* b, double* x, cudaStream_t st);
+void launch_refine_residual(const ProblemDev& P, cudaStream_t st);
+void launch_update(const ProblemDev& P, int k, cudaStream_t st);
+void launch_eval_x0(const ModelHost& m, const GridHost& g, const ProblemDev& P, int k,
+                    cudaStream_t st);
+void launch_eval_points(const ModelHost& m, const GridHost& g, const ProblemDev& P, int q,
+                        const double* t, const double* x, double* price, double* dudx,
+                        cudaStream_t st);
+size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed);
+int paths_supported_d(int d);

@@ -1,0 +1,422 @@
+// k_linalg.cu -- the least-squares refit of Algorithm 2 (eq. alpha) through
+// the normal equations A alpha = sum_i y_i B(t_i, x_i) (eq. alphasys,
+// Section 3.2.2), in the correction form alpha^{k+1} = alpha^k + delta with
+// A delta = B^T c^k (the fit of u^k + c^k equals alpha^k plus the fit of c^k
+// because u^k lies in the span of the basis).  The paper solves with LAPACK
+// dgelsy; here the Gram matrix is factored by an FP64 Cholesky on the GPU,
+// with an optional FP64 iterative refinement of the normal equations.
+// Also: the per-point reduction of eq. chat, the coefficient update and the
+// price / delta read-out of Section 4.3.
+#include "common.cuh"
+
+namespace {
+
+// eq. chat: c_i = (1/M) sum of the per-chunk sums, in chunk order
+__global__ void k_reduce_c(int n, int chunks, int M, const double* __restrict__ partial,
+                           double* __restrict__ c) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int q = 0; q < chunks; ++q) s += partial[(size_t)i * chunks + q];
+  c[i] = s / (double)M;
+}
+
+// warp per basis function: out[l] = sum_i B[l][i] y[i] (fixed lane order
+// and shuffle tree); with sub != nullptr, out[l] = sub[l] - that sum
+__global__ void k_bt_times(int n, int n_pad, int p, const double* __restrict__ B,
+                           const double* __restrict__ y, const double* __restrict__ sub,
+                           double* __restrict__ out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= p) return;
+  const double* row = B + (size_t)warp * n_pad;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += row[i] * y[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[warp] = sub ? (sub[warp] - s) : s;
+}
+
+// thread per point: v[i] = sum_l B[l][i] x[l]
+__global__ void k_b_times(int n, int n_pad, int p, const double* __restrict__ B,
+                          const double* __restrict__ x, double* __restrict__ v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int l = 0; l < p; ++l) s += B[(size_t)l * n_pad + i] * x[l];
+  v[i] = s;
+}
+
+// FP64 Gram A = B B^T on CUDA cores: one 32x32 upper tile per CTA, written
+// to both triangles.
+__global__ void __launch_bounds__(256) k_gram_f64(int n, int n_pad, int p,
+                                                  const double* __restrict__ B,
+                                                  double* __restrict__ A) {
+  __shared__ double As[32][33], Bs[32][33];
+  // decode the upper tile (ti <= tj) from blockIdx.x
+  const int T = (p + 31) / 32;
+  int t = blockIdx.x, ti = 0;
+  while (t >= T - ti) {
+    t -= T - ti;
+    ++ti;
+  }
+  const int tj = ti + t;
+  const int r0 = ti * 32, c0 = tj * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+      const int rr = q >> 5, kk = q & 31;
+      const int kg = k0 + kk;
+      As[rr][kk] = (r0 + rr < p && kg < n) ? B[(size_t)(r0 + rr) * n_pad + kg] : 0.0;
+      Bs[rr][kk] = (c0 + rr < p && kg < n) ? B[(size_t)(c0 + rr) * n_pad + kg] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const double b = Bs[tx][kk];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += As[ty + 8 * q][kk] * b;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = r0 + ty + 8 * q, c = c0 + tx;
+    if (r < p && c < p) {
+      A[(size_t)r * p + c] = acc[q];
+      A[(size_t)c * p + r] = acc[q];
+    }
+  }
+}
+
+// original diagonal of A, for the relative pivot test of the factorisation
+__global__ void k_save_diag(const double* __restrict__ A, int p, double* __restrict__ diag0) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < p) diag0[j] = A[(size_t)j * p + j];
+}
+
+// Right-looking blocked Cholesky, panel width 32, lower factor in place.
+// Panel step 1: one CTA factors the 32x32 diagonal block in shared memory.
+// A pivot below 1e-13 of its original diagonal entry (or not finite) marks
+// the matrix as numerically singular: ST_NOT_PD, and the pivot becomes NaN.
+__global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ A, int p, int j0,
+                                                   int* __restrict__ status,
+                                                   const double* __restrict__ diag0) {
+  __shared__ double Dg[32][33];
+  const int nb = min(32, p - j0);
+  const int tid = threadIdx.x;
+  for (int q = tid; q < 32 * 32; q += 256) {
+    const int r = q >> 5, c = q & 31;
+    Dg[r][c] = (r < nb && c < nb && c <= r) ? A[(size_t)(j0 + r) * p + (j0 + c)] : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (tid == 0) {
+      const double piv = Dg[c][c];
+      if (!(piv > 1e-13 * diag0[j0 + c]) || !isfinite(piv)) {
+        atomicOr(status, ST_NOT_PD);
+        Dg[c][c] = nan("");
+      } else {
+        Dg[c][c] = sqrt(piv);
+      }
+    }
+    __syncthreads();
+    if (tid > c && tid < nb) Dg[tid][c] /= Dg[c][c];
+    __syncthreads();
+    for (int q = tid; q < 32 * 32; q += 256) {
+      const int r = q >> 5, s2 = q & 31;
+      if (s2 > c && r >= s2 && r < nb) Dg[r][s2] -= Dg[r][c] * Dg[s2][c];
+    }
+    __syncthreads();
+  }
+  for (int q = tid; q < 32 * 32; q += 256) {
+    const int r = q >> 5, c = q & 31;
+    if (r < nb && c <= r) A[(size_t)(j0 + r) * p + (j0 + c)] = Dg[r][c];
+  }
+}
+
+// Panel step 2: rows below the diagonal block solve x L_jj^T = a (forward
+// substitution), one thread per row.
+__global__ void __launch_bounds__(32) k_chol_trsm(double* __restrict__ A, int p, int j0) {
+  __shared__ double Dg[32][33];
+  const int nb = min(32, p - j0);
+  for (int q = threadIdx.x; q < 32 * 32; q += 32) {
+    const int r = q >> 5, c = q & 31;
+    Dg[r][c] = (r < nb && c < nb && c <= r) ? A[(size_t)(j0 + r) * p + (j0 + c)] : 0.0;
+  }
+  __syncthreads();
+  const int row = j0 + nb + 32 * blockIdx.x + threadIdx.x;
+  if (row >= p) return;
+  double xr[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) xr[c] = (c < nb) ? A[(size_t)row * p + j0 + c] : 0.0;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c < nb) {
+      double acc = xr[c];
+#pragma unroll
+      for (int q = 0; q < c; ++q) acc -= xr[q] * Dg[c][q];
+      xr[c] = acc / Dg[c][c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c)
+    if (c < nb) A[(size_t)row * p + j0 + c] = xr[c];
+}
+
+// trailing update A22 -= L21 L21^T on the lower triangle, 32x32 tiles
+__global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ A, int p, int j0) {
+  __shared__ double Lr[32][33], Lc[32][33];
+  const int nb = min(32, p - j0);
+  const int base = j0 + nb;
+  const int m = p - base;
+  const int T = (m + 31) / 32;
+  int t = blockIdx.x, ti = 0;  // lower tiles (tj <= ti), row-major
+  while (t > ti) {
+    t -= ti + 1;
+    ++ti;
+  }
+  const int tj = t;
+  if (ti >= T) return;
+  const int r0 = base + 32 * ti, c0 = base + 32 * tj;
+  for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+    const int rr = q >> 5, kk = q & 31;
+    Lr[rr][kk] = (r0 + rr < p && kk < nb) ? A[(size_t)(r0 + rr) * p + j0 + kk] : 0.0;
+    Lc[rr][kk] = (c0 + rr < p && kk < nb) ? A[(size_t)(c0 + rr) * p + j0 + kk] : 0.0;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int rr = ty + 8 * q;
+    const int r = r0 + rr, c = c0 + tx;
+    if (r < p && c < p && c <= r) {
+      double s = 0.0;
+#pragma unroll 8
+      for (int kk = 0; kk < 32; ++kk) s += Lr[rr][kk] * Lc[tx][kk];
+      A[(size_t)r * p + c] -= s;
+    }
+  }
+}
+
+// x (+)= A^{-1} b with the Cholesky factor in the lower triangle of A:
+// forward then backward substitution, column-oriented, one CTA.
+__global__ void __launch_bounds__(1024) k_chol_solve(const double* __restrict__ A, int p,
+                                                     const double* __restrict__ b,
+                                                     double* __restrict__ x, int accumulate,
+                                                     double* __restrict__ work) {
+  const int tid = threadIdx.x;
+  for (int r = tid; r < p; r += blockDim.x) work[r] = b[r];
+  __syncthreads();
+  __shared__ double piv;
+  for (int c = 0; c < p; ++c) {
+    if (tid == 0) {
+      work[c] /= A[(size_t)c * p + c];
+      piv = work[c];
+    }
+    __syncthreads();
+    const double yc = piv;
+    for (int r = c + 1 + tid; r < p; r += blockDim.x) work[r] -= A[(size_t)r * p + c] * yc;
+    __syncthreads();
+  }
+  for (int c = p - 1; c >= 0; --c) {
+    if (tid == 0) {
+      work[c] /= A[(size_t)c * p + c];
+      piv = work[c];
+    }
+    __syncthreads();
+    const double xc = piv;
+    for (int r = tid; r < c; r += blockDim.x) work[r] -= A[(size_t)c * p + r] * xc;
+    __syncthreads();
+  }
+  for (int r = tid; r < p; r += blockDim.x) x[r] = accumulate ? (x[r] + work[r]) : work[r];
+}
+
+// alpha += delta; ||delta||_2, ||delta||_inf into the report block; FP32 copy
+__global__ void __launch_bounds__(256) k_update(int p, int k, double* __restrict__ alpha,
+                                                float* __restrict__ alpha32,
+                                                const double* __restrict__ delta,
+                                                double* __restrict__ out) {
+  __shared__ double s2[256], si[256];
+  double a2 = 0.0, ai = 0.0;
+  for (int l = threadIdx.x; l < p; l += 256) {
+    const double dl = delta[l];
+    const double al = alpha[l] + dl;
+    alpha[l] = al;
+    if (alpha32) alpha32[l] = (float)al;
+    a2 += dl * dl;
+    ai = fmax(ai, fabs(dl));
+  }
+  s2[threadIdx.x] = a2;
+  si[threadIdx.x] = ai;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+      si[threadIdx.x] = fmax(si[threadIdx.x], si[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && k >= 0 && k < 64) {
+    out[OUT_RES2 + k] = sqrt(s2[0]);
+    out[OUT_RESI + k] = si[0];
+  }
+}
+
+struct EvalArgs {
+  int d, p, n_query;
+  double ctr[BSDE_DMAX + 1], sc[BSDE_DMAX + 1];
+};
+
+// u and du/dx_j at query points (Section 4.3: price V = u, Delta = grad_x V):
+// one CTA per point, threads over basis functions, fixed-order reduction.
+__global__ void __launch_bounds__(256) k_eval(const __grid_constant__ EvalArgs ea,
+                                              const double* __restrict__ alpha,
+                                              const uint2* __restrict__ pairs,
+                                              const uint8_t* __restrict__ nnz,
+                                              const double* __restrict__ qt,
+                                              const double* __restrict__ qx,
+                                              double* __restrict__ price,
+                                              double* __restrict__ dudx) {
+  __shared__ double red[256][BSDE_DMAX + 1];
+  const int qi = blockIdx.x;
+  const int d = ea.d;
+  double xi[BSDE_DMAX + 1];
+  xi[0] = (qt[qi] - ea.ctr[0]) * ea.sc[0];
+  for (int j = 0; j < d; ++j) xi[j + 1] = (qx[(size_t)qi * d + j] - ea.ctr[j + 1]) * ea.sc[j + 1];
+  double u = 0.0, g[BSDE_DMAX];
+  for (int j = 0; j < d; ++j) g[j] = 0.0;
+  for (int l = threadIdx.x; l < ea.p; l += 256) {
+    const uint2 pr = pairs[l];
+    const int nz = nnz[l];
+    double tv[BSDE_NNZ_MAX], dv[BSDE_NNZ_MAX];
+    int var[BSDE_NNZ_MAX];
+    for (int a = 0; a < nz; ++a) {
+      const uint32_t byte = ((a < 4 ? pr.x >> (8 * a) : pr.y >> (8 * (a - 4)))) & 0xffu;
+      const int v = (int)(byte >> 4), e = (int)(byte & 15u);
+      const double z = xi[v];
+      double t0 = 1.0, t1 = z, d0 = 0.0, d1 = 1.0;
+      for (int q = 2; q <= e; ++q) {
+        const double t2 = 2.0 * z * t1 - t0, d2 = 2.0 * t1 + 2.0 * z * d1 - d0;
+        t0 = t1; t1 = t2; d0 = d1; d1 = d2;
+      }
+      tv[a] = t1;
+      dv[a] = d1;
+      var[a] = v;
+    }
+    double val = 1.0;
+    for (int a = 0; a < nz; ++a) val *= tv[a];
+    u += alpha[l] * val;
+    for (int a = 0; a < nz; ++a) {
+      if (var[a] == 0) continue;
+      double gd = dv[a];
+      for (int c = 0; c < nz; ++c)
+        if (c != a) gd *= tv[c];
+      g[var[a] - 1] += alpha[l] * gd * ea.sc[var[a]];
+    }
+  }
+  red[threadIdx.x][0] = u;
+  for (int j = 0; j < d; ++j) red[threadIdx.x][j + 1] = g[j];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int j = 0; j <= d; ++j) red[threadIdx.x][j] += red[threadIdx.x + o][j];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    price[qi] = red[0][0];
+    if (dudx)
+      for (int j = 0; j < d; ++j) dudx[(size_t)qi * d + j] = red[0][j + 1];
+  }
+}
+
+// read-out point (0, log S0) written into the report block
+__global__ void k_x0(int d, double t0, const double* __restrict__ logS0, double* __restrict__ qt,
+                     double* __restrict__ qx) {
+  if (threadIdx.x == 0) qt[0] = t0;
+  if (threadIdx.x < d) qx[threadIdx.x] = logS0[threadIdx.x];
+}
+
+__global__ void k_copy_price(int k, int d, double* __restrict__ out) {
+  // out[OUT_PRICE] and dudx were written by k_eval; keep the per-iteration price
+  if (threadIdx.x == 0 && k >= 0 && k < 64) out[OUT_PRICE_IT + k] = out[OUT_PRICE];
+}
+
+}  // namespace
+
+void launch_reduce_c(const ProblemDev& P, int M, cudaStream_t st) {
+  k_reduce_c<<<(P.n + 255) / 256, 256, 0, st>>>(P.n, P.chunks, M, P.partial, P.c);
+}
+
+void launch_gram_f64(const ProblemDev& P, cudaStream_t st) {
+  const int T = (P.p + 31) / 32;
+  k_gram_f64<<<T * (T + 1) / 2, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.A);
+}
+
+void launch_rhs(const ProblemDev& P, cudaStream_t st) {
+  k_bt_times<<<(P.p * 32 + 255) / 256, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.c, nullptr, P.rhs);
+}
+
+void launch_cholesky(const ProblemDev& P, cudaStream_t st) {
+  // P.v (n >= p entries) holds the original diagonal during the factorisation
+  k_save_diag<<<(P.p + 255) / 256, 256, 0, st>>>(P.A, P.p, P.v);
+  for (int j0 = 0; j0 < P.p; j0 += 32) {
+    k_chol_diag<<<1, 256, 0, st>>>(P.A, P.p, j0, P.status, P.v);
+    const int m = P.p - j0 - 32;
+    if (m > 0) {
+      k_chol_trsm<<<(m + 31) / 32, 32, 0, st>>>(P.A, P.p, j0);
+      const int T = (m + 31) / 32;
+      k_chol_update<<<T * (T + 1) / 2, 256, 0, st>>>(P.A, P.p, j0);
+    }
+  }
+}
+
+void launch_chol_solve(const ProblemDev& P, const double* b, double* x, cudaStream_t st) {
+  // work vector: the residual buffer is free at this point when b != res;
+  // use v (n >= p) as scratch
+  k_chol_solve<<<1, 1024, 0, st>>>(P.A, P.p, b, x, b == P.res ? 1 : 0, P.v);
+}
+
+void launch_refine_residual(const ProblemDev& P, cudaStream_t st) {
+  k_b_times<<<(P.n + 255) / 256, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.delta, P.v);
+  k_bt_times<<<(P.p * 32 + 255) / 256, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.v, P.rhs, P.res);
+}
+
+void launch_update(const ProblemDev& P, int k, cudaStream_t st) {
+  k_update<<<1, 256, 0, st>>>(P.p, k, P.alpha, P.alpha32, P.delta, P.out);
+}
+
+static EvalArgs eval_args(const ModelHost& m, const GridHost& g, const ProblemDev& P, int q) {
+  EvalArgs ea;
+  memset(&ea, 0, sizeof(ea));
+  ea.d = m.d;
+  ea.p = P.p;
+  ea.n_query = q;
+  for (int v = 0; v <= m.d; ++v) {
+    ea.ctr[v] = 0.5 * (g.lo[v] + g.hi[v]);
+    ea.sc[v] = 2.0 / (g.hi[v] - g.lo[v]);
+  }
+  return ea;
+}
+
+// price and du/dx at (0, log S0) after iteration k; the query point lives in
+// the tail of the report block (OUT_SIZE .. OUT_SIZE + 1 + 2 d)
+void launch_eval_x0(const ModelHost& m, const GridHost& g, const ProblemDev& P, int k,
+                    cudaStream_t st) {
+  double* qt = P.out + OUT_SIZE;
+  double* qx = qt + 1;
+  double* logS0 = qx + BSDE_DMAX;
+  k_x0<<<1, 32, 0, st>>>(m.d, 0.0, logS0, qt, qx);
+  const EvalArgs ea = eval_args(m, g, P, 1);
+  k_eval<<<1, 256, 0, st>>>(ea, P.alpha, P.pairs, P.nnz, qt, qx, P.out + OUT_PRICE,
+                            P.out + OUT_DUDX);
+  k_copy_price<<<1, 32, 0, st>>>(k, m.d, P.out);
+}
+
+void launch_eval_points(const ModelHost& m, const GridHost& g, const ProblemDev& P, int q,
+                        const double* t, const double* x, double* price, double* dudx,
+                        cudaStream_t st) {
+  const EvalArgs ea = eval_args(m, g, P, q);
+  k_eval<<<q, 256, 0, st>>>(ea, P.alpha, P.pairs, P.nnz, t, x, price, dudx);
+}

@@ -1,0 +1,433 @@
+// k_paths.cuh -- the hot kernel of Algorithm 2: for every point (t_i, x_i)
+// and every path m, the Monte Carlo sample
+//     a_m = (T - t_i) g1(tau, X_tau) + Phi(X_T) - u^k(T, X_T),
+//     g1  = f(tau, X_tau, u^k) + d_t u^k + L^N u^k,   f(t,x,y) = -r y + lambda (Phi - y)^+
+// (eq. psiN with g1 = f_{u^k} + (d_t + L^N) u^k and g2 = Phi - u^k, Section 3.1;
+// penalised driver of eq. bsde-penal-2), summed per point.
+//
+// GB300 mapping: one CTA per (point, chunk of paths); each thread runs PPT
+// paths one after the other, keeping the d-dimensional state in registers
+// (D is a template parameter, so every per-asset loop is unrolled).  The
+// normals of the Euler steps come from Philox4x32-10 in groups of G steps
+// whose G*D normals are a whole number of Philox blocks, so the counter of
+// every normal is a compile-time offset.  The time factors of the local
+// volatility, the coefficients alpha and the multi-index table are staged
+// in shared memory once per CTA.  The random time tau falls inside step s*;
+// the main loop only records X_{s*} and the step's increment, and X_tau is
+// drawn after the loop through a Brownian bridge (no divergent branch in
+// the loop).  u^k and its derivatives at (tau, X_tau) and u^k(T, X_T) come
+// from per-thread Chebyshev tables in shared memory (layout [slot][thread],
+// conflict-free).  Per-path samples are accumulated in FP64; the CTA
+// reduces them by a fixed warp-shuffle tree into partial[i][chunk], so the
+// result does not depend on scheduling.
+#pragma once
+#include "common.cuh"
+
+namespace paths {
+
+enum { VK_CONST = 0, VK_TANH = 1, VK_DUPIRE = 2 };
+
+template <typename R, int D>
+struct Args {
+  R T, r, lam, K, s_dupire;
+  R rd[D];          // r - delta_j
+  R w[D], va[D], kappa[D];
+  R L[D][D];        // lower Cholesky factor of the correlation
+  R Cp[D + 1][D + 1];  // correlation padded with a zero time row/column
+  R ctr[D + 1], sc[D + 1];  // xi_v = (y_v - ctr_v) sc_v
+  int N, M, n, p, eta, chunks, tpb, ppt, tab_stride;
+  int payoff, obstacle, absflag, vol_sin;
+  R vb;
+  uint32_t k;
+  const uint32_t* key;
+  const double* pt;
+  const double* px;
+  const R* alpha;
+  const uint2* pairs;
+  const uint8_t* nnz;
+  double* partial;
+};
+
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+template <typename R>
+__device__ __forceinline__ R uniform_frac(uint32_t w);
+template <>
+__device__ __forceinline__ float uniform_frac<float>(uint32_t w) {
+  return fmaf(__uint2float_rn(w), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+}
+template <>
+__device__ __forceinline__ double uniform_frac<double>(uint32_t w) {
+  return ((double)w + 0.5) * 2.3283064365386962890625e-10;
+}
+
+// local volatility of asset j at the step whose table row is tabs
+template <int VK, typename R, int D>
+__device__ __forceinline__ R sigma_j(const Args<R, D>& a, const R* tabs, int j, R xj) {
+  if constexpr (VK == VK_CONST) {
+    return a.va[j];
+  } else if constexpr (VK == VK_TANH) {
+    R th = Math<R>::tanh(xj - a.kappa[j]);
+    if (a.absflag) th = Math<R>::fabs(th);
+    return a.va[j] + tabs[j] * th;
+  } else {
+    const R dev = Math<R>::exp(xj) * tabs[2] - a.s_dupire;
+    return tabs[0] - tabs[1] * Math<R>::exp(R(-0.001) * dev * dev);
+  }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ R basket_value(const Args<R, D>& a, const R* x, bool positive) {
+  R s = 0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) s += a.w[j] * Math<R>::exp(x[j]);
+  const R v = (a.payoff == 0) ? (a.K - s) : (s - a.K);
+  return positive ? Math<R>::fmax(v, R(0)) : v;
+}
+
+// contribution of one basis function with NZ active variates
+template <int NZ, typename R>
+__device__ __forceinline__ void term(const R* __restrict__ tb, int S, int eta, int tpb, int tid,
+                                     uint2 pr, const R* __restrict__ Cp, int dp, R al, R& u,
+                                     R& g, R& uT) {
+  if constexpr (NZ == 0) {
+    u += al;
+    uT += al;
+  } else {
+    R tv[NZ], td[NZ], s1[NZ], s2[NZ], tt[NZ];
+    int var[NZ];
+#pragma unroll
+    for (int a = 0; a < NZ; ++a) {
+      const uint32_t byte = (a < 4 ? (pr.x >> (8 * a)) : (pr.y >> (8 * (a - 4)))) & 0xffu;
+      const int v = (int)(byte >> 4), e = (int)(byte & 15u);
+      var[a] = v;
+      const int base = (v * eta + e - 1) * tpb + tid;
+      tv[a] = tb[base];
+      td[a] = tb[base + S];
+      s1[a] = tb[base + 2 * S];
+      s2[a] = tb[base + 3 * S];
+      tt[a] = tb[base + 4 * S];
+    }
+    R pre[NZ + 1], suf[NZ + 1];
+    pre[0] = R(1);
+    suf[NZ] = R(1);
+#pragma unroll
+    for (int a = 0; a < NZ; ++a) pre[a + 1] = pre[a] * tv[a];
+#pragma unroll
+    for (int a = NZ - 1; a >= 0; --a) suf[a] = suf[a + 1] * tv[a];
+    R valT = tt[0];
+#pragma unroll
+    for (int a = 1; a < NZ; ++a) valT *= tt[a];
+    R gen = 0;
+#pragma unroll
+    for (int a = 0; a < NZ; ++a) {
+      const R ex = pre[a] * suf[a + 1];
+      gen += (td[a] + R(0.5) * s2[a]) * ex;
+    }
+#pragma unroll
+    for (int a = 0; a < NZ; ++a) {
+#pragma unroll
+      for (int b = a + 1; b < NZ; ++b) {
+        R ex2 = R(1);
+#pragma unroll
+        for (int c = 0; c < NZ; ++c)
+          if (c != a && c != b) ex2 *= tv[c];
+        gen += Cp[var[a] * dp + var[b]] * s1[a] * s1[b] * ex2;
+      }
+    }
+    u += al * pre[NZ];
+    g += al * gen;
+    uT += al * valT;
+  }
+}
+
+template <int VK, typename R, int D>
+__global__ void __launch_bounds__(256) k_paths(const __grid_constant__ Args<R, D> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int DP = D + 1;
+  const int tid = threadIdx.x;
+  const int tpb = a.tpb;
+  const int item = blockIdx.x;
+  const int i = item / a.chunks;
+  const int chunk = item - i * a.chunks;
+
+  // shared memory carve-up
+  R* tab = reinterpret_cast<R*>(smem_raw);                         // N x tab_stride
+  R* s_alpha = tab + (size_t)a.N * a.tab_stride;                   // p
+  R* s_cp = s_alpha + a.p;                                          // DP x DP
+  size_t off = ((size_t)a.N * a.tab_stride + a.p + DP * DP) * sizeof(R);
+  off = (off + 15) & ~(size_t)15;
+  uint2* s_pairs = reinterpret_cast<uint2*>(smem_raw + off);
+  off += (size_t)a.p * sizeof(uint2);
+  uint8_t* s_nnz = smem_raw + off;
+  off += ((size_t)a.p + 15) & ~(size_t)15;
+  R* cheb = reinterpret_cast<R*>(smem_raw + off);                  // 5 x DP x eta x tpb
+  const int S = DP * a.eta * tpb;
+  off += (size_t)5 * S * sizeof(R);
+  off = (off + 15) & ~(size_t)15;
+  double* red = reinterpret_cast<double*>(smem_raw + off);          // 32
+
+  const R ti = (R)a.pt[i];
+  R x0[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) x0[j] = (R)a.px[(size_t)j * a.n + i];
+  const R h = (a.T - ti) / (R)a.N;
+  const R sqh = Math<R>::sqrt(h);
+
+  // per-step time factors of the local volatility
+  for (int idx = tid; idx < a.N * a.tab_stride; idx += tpb) {
+    const int s = idx / a.tab_stride, j = idx - s * a.tab_stride;
+    const double ts = (double)ti + (double)s * (double)h;
+    R v = 0;
+    if constexpr (VK == VK_TANH) {
+      v = a.vol_sin ? (R)((double)a.vb * sin((double)(j + 1) + ts)) : (R)((double)a.vb * exp(-ts));
+    } else if constexpr (VK == VK_DUPIRE) {
+      const double ew = exp(-0.05 * sqrt(ts));
+      v = (j == 0) ? (R)(0.72 * ew) : (j == 1) ? (R)(0.6 * exp(-0.1 * ts) * ew) : (R)exp((double)a.r * ts);
+    }
+    tab[idx] = v;
+  }
+  for (int l = tid; l < a.p; l += tpb) {
+    s_alpha[l] = a.alpha[l];
+    s_pairs[l] = a.pairs[l];
+    s_nnz[l] = a.nnz[l];
+  }
+  for (int q = tid; q < DP * DP; q += tpb) s_cp[q] = (&a.Cp[0][0])[q];
+  __syncthreads();
+
+  const Philox ph{a.key[0], a.key[1]};
+  const uint32_t tagU = (TAG_U << 24) | a.k, tagZ = (TAG_Z << 24) | a.k, tagB = (TAG_B << 24) | a.k;
+  constexpr int G = 4 / gcd_c(D, 4);  // steps per group: G*D normals = whole Philox blocks
+  constexpr int NB = G * D / 4;
+  constexpr int NBB = (D + 3) / 4;
+  const int ppc = tpb * a.ppt;
+  double acc = 0.0;
+
+  for (int jp = 0; jp < a.ppt; ++jp) {
+    const int m = chunk * ppc + jp * tpb + tid;
+    if (m >= a.M) break;
+    // the uniform random time: U = (s* + theta) / N from one 32-bit word
+    const uint4 ou = ph(0u, (uint32_t)m, (uint32_t)i, tagU);
+    const uint64_t wN = (uint64_t)ou.x * (uint64_t)a.N;
+    const int sstar = (int)(wN >> 32);
+    const R theta = uniform_frac<R>((uint32_t)wN);
+
+    R X[D], Xs[D], dXs[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      X[j] = x0[j];
+      Xs[j] = x0[j];
+      dXs[j] = 0;
+    }
+    for (int s0 = 0; s0 < a.N; s0 += G) {
+      R z[G * D];
+      const uint32_t blk0 = (uint32_t)(s0 / G) * (uint32_t)NB;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const uint4 o = ph(blk0 + b, (uint32_t)m, (uint32_t)i, tagZ);
+        Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1]);
+        Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3]);
+      }
+#pragma unroll
+      for (int gs = 0; gs < G; ++gs) {
+        const int s = s0 + gs;
+        if (s < a.N) {
+          const R* tabs = tab + s * a.tab_stride;
+          const bool hit = (s == sstar);
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            R y = 0;
+#pragma unroll
+            for (int q = 0; q <= j; ++q) y += a.L[j][q] * z[gs * D + q];
+            const R sig = sigma_j<VK>(a, tabs, j, X[j]);
+            const R drift = a.rd[j] - R(0.5) * sig * sig;
+            const R dx = drift * h + sig * sqh * y;
+            if (hit) {
+              Xs[j] = X[j];
+              dXs[j] = dx;
+            }
+            X[j] += dx;
+          }
+        }
+      }
+    }
+
+    // X at tau: Brownian bridge inside step s*, coefficients frozen at t_{s*}
+    R zb[NBB * 4];
+#pragma unroll
+    for (int b = 0; b < NBB; ++b) {
+      const uint4 o = ph((uint32_t)b, (uint32_t)m, (uint32_t)i, tagB);
+      Math<R>::box_muller(o.x, o.y, zb[4 * b + 0], zb[4 * b + 1]);
+      Math<R>::box_muller(o.z, o.w, zb[4 * b + 2], zb[4 * b + 3]);
+    }
+    const R* tab_s = tab + sstar * a.tab_stride;
+    const R bb = Math<R>::sqrt(theta * (R(1) - theta) * h);
+    R Xtau[D], sig_s[D], drift_s[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      R y = 0;
+#pragma unroll
+      for (int q = 0; q <= j; ++q) y += a.L[j][q] * zb[q];
+      sig_s[j] = sigma_j<VK>(a, tab_s, j, Xs[j]);
+      drift_s[j] = a.rd[j] - R(0.5) * sig_s[j] * sig_s[j];
+      Xtau[j] = Xs[j] + theta * dXs[j] + sig_s[j] * bb * y;
+    }
+    const R tau = ti + ((R)sstar + theta) * h;
+
+    // per-thread Chebyshev tables: value, drift- and diffusion-scaled
+    // derivatives at (tau, X_tau), value at (T, X_T)
+    R* tb = cheb + tid;
+#pragma unroll
+    for (int v = 0; v < DP; ++v) {
+      const R xi = (v == 0) ? (tau - a.ctr[0]) * a.sc[0] : (Xtau[v - 1] - a.ctr[v]) * a.sc[v];
+      const R xT = (v == 0) ? (a.T - a.ctr[0]) * a.sc[0] : (X[v - 1] - a.ctr[v]) * a.sc[v];
+      const R bt = (v == 0) ? a.sc[0] : drift_s[v - 1] * a.sc[v];
+      const R st = (v == 0) ? R(0) : sig_s[v - 1] * a.sc[v];
+      R t0 = 1, t1 = xi, d0 = 0, d1 = 1, e0 = 0, e1 = 0, T0 = 1, T1 = xT;
+      for (int e = 1; e <= a.eta; ++e) {
+        if (e >= 2) {
+          const R t2 = R(2) * xi * t1 - t0;
+          const R d2 = R(2) * t1 + R(2) * xi * d1 - d0;
+          const R e2 = R(4) * d1 + R(2) * xi * e1 - e0;
+          const R T2 = R(2) * xT * T1 - T0;
+          t0 = t1; t1 = t2; d0 = d1; d1 = d2; e0 = e1; e1 = e2; T0 = T1; T1 = T2;
+        }
+        const int base = (v * a.eta + e - 1) * tpb;
+        tb[base] = t1;
+        tb[base + S] = bt * d1;
+        tb[base + 2 * S] = st * d1;
+        tb[base + 3 * S] = st * st * e1;
+        tb[base + 4 * S] = T1;
+      }
+    }
+    R u = 0, gsum = 0, uT = 0;
+    const R* tbr = cheb;
+    for (int l = 0; l < a.p; ++l) {
+      const R al = s_alpha[l];
+      const uint2 pr = s_pairs[l];
+      switch (s_nnz[l]) {
+        case 0: term<0, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        case 1: term<1, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        case 2: term<2, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        case 3: term<3, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        case 4: term<4, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        case 5: term<5, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        case 6: term<6, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        case 7: term<7, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        default: term<8, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+      }
+    }
+    const R obs = basket_value<R, D>(a, Xtau, a.obstacle == 0);
+    const R f = -a.r * u + a.lam * Math<R>::fmax(obs - u, R(0));
+    const R phiT = basket_value<R, D>(a, X, true);
+    const R am = (a.T - ti) * (f + gsum) + phiT - uT;
+    acc += (double)am;
+  }
+
+  // fixed-order CTA reduction of the per-thread sums
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const int warp = tid >> 5, lane = tid & 31;
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int wv = 0; wv < (tpb >> 5); ++wv) s += red[wv];
+    a.partial[(size_t)i * a.chunks + chunk] = s;
+  }
+}
+
+inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize) {
+  const int dp = d + 1;
+  const int tab_stride = d < 3 ? 3 : d;
+  size_t off = ((size_t)N * tab_stride + p + dp * dp) * rsize;
+  off = (off + 15) & ~(size_t)15;
+  off += (size_t)p * sizeof(uint2);
+  off += ((size_t)p + 15) & ~(size_t)15;
+  off += (size_t)5 * dp * eta * tpb * rsize;
+  off = (off + 15) & ~(size_t)15;
+  off += 32 * sizeof(double);
+  return off;
+}
+
+template <typename R, int D>
+cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, int M, int N,
+                   uint32_t k, int tpb, int ppt, cudaStream_t st) {
+  Args<R, D> a;
+  memset(&a, 0, sizeof(a));
+  a.T = (R)m.T;
+  a.r = (R)m.r;
+  a.lam = (R)m.lambda;
+  a.K = (R)m.K;
+  a.s_dupire = (R)m.s_dupire;
+  a.vb = (R)m.b;
+  for (int j = 0; j < D; ++j) {
+    a.rd[j] = (R)(m.r - m.div[j]);
+    a.w[j] = (R)m.w[j];
+    a.va[j] = (R)m.a[j];
+    a.kappa[j] = (R)m.kappa[j];
+    for (int q = 0; q < D; ++q) {
+      a.L[j][q] = (R)m.L[j * D + q];
+      a.Cp[j + 1][q + 1] = (R)m.C[j * D + q];
+    }
+  }
+  for (int v = 0; v <= D; ++v) {
+    a.ctr[v] = (R)(0.5 * (g.lo[v] + g.hi[v]));
+    a.sc[v] = (R)(2.0 / (g.hi[v] - g.lo[v]));
+  }
+  a.N = N;
+  a.M = M;
+  a.n = P.n;
+  a.p = P.p;
+  a.eta = P.eta < 1 ? 1 : P.eta;
+  a.tpb = tpb;
+  a.ppt = ppt;
+  a.chunks = P.chunks;
+  a.tab_stride = D < 3 ? 3 : D;
+  a.payoff = m.payoff;
+  a.obstacle = m.obstacle;
+  a.absflag = (m.vol_kind == 1) ? 1 : 0;
+  a.vol_sin = (m.vol_kind == 2) ? 1 : 0;
+  a.k = k;
+  a.key = P.key;
+  a.pt = P.t;
+  a.px = P.x;
+  if constexpr (sizeof(R) == 4)
+    a.alpha = reinterpret_cast<const R*>(P.alpha32);
+  else
+    a.alpha = reinterpret_cast<const R*>(P.alpha);
+  a.pairs = P.pairs;
+  a.nnz = P.nnz;
+  a.partial = P.partial;
+  const size_t smem = smem_bytes(D, P.p, a.eta, N, tpb, sizeof(R));
+  const int vk = (m.vol_kind == 0) ? VK_CONST : (m.vol_kind == 3) ? VK_DUPIRE : VK_TANH;
+  const unsigned grid = (unsigned)P.n * (unsigned)P.chunks;
+  cudaError_t err = cudaSuccess;
+  if (vk == VK_CONST) {
+    err = cudaFuncSetAttribute(k_paths<VK_CONST, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (err != cudaSuccess) return err;
+    k_paths<VK_CONST, R, D><<<grid, tpb, smem, st>>>(a);
+  } else if (vk == VK_TANH) {
+    err = cudaFuncSetAttribute(k_paths<VK_TANH, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (err != cudaSuccess) return err;
+    k_paths<VK_TANH, R, D><<<grid, tpb, smem, st>>>(a);
+  } else {
+    err = cudaFuncSetAttribute(k_paths<VK_DUPIRE, R, D>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_paths<VK_DUPIRE, R, D><<<grid, tpb, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace paths
+
+#define BSDE_PATHS_INSTANTIATE(DV)                                                           \
+  cudaError_t launch_paths_d##DV(const ModelHost& m, const GridHost& g, const ProblemDev& P, \
+                                 int M, int N, uint32_t k, bool mixed, int tpb, int ppt,     \
+                                 cudaStream_t st) {                                          \
+    return mixed ? paths::launch<float, DV>(m, g, P, M, N, k, tpb, ppt, st)                  \
+                 : paths::launch<double, DV>(m, g, P, M, N, k, tpb, ppt, st);                \
+  }

@@ -1,0 +1,15 @@
+// multiindex.h -- host-side multi-index sets of the polynomial basis.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+// multi-indices in N^dp with total degree <= eta (q >= 1) or hyperbolic
+// pseudo-norm <= eta (q < 1), graded, lexicographically descending
+std::vector<std::vector<int>> build_multi_indices(int dp, int eta, double q);
+
+// pack each multi-index as (variate << 4 | degree) bytes in increasing
+// variate order, two 32-bit words per basis function; false when a variate
+// or degree exceeds 15 or more than 8 variates are active
+bool pack_multi_indices(const std::vector<std::vector<int>>& nus, std::vector<uint32_t>& pairs_xy,
+                        std::vector<uint8_t>& nnz, int& max_deg);

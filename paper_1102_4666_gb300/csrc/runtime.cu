@@ -1,0 +1,545 @@
+// runtime.cu -- host runtime of one resident BSDE problem (see runtime.h).
+#include "runtime.h"
+
+#include <cmath>
+#include <cstring>
+#include <sstream>
+
+#include "multiindex.h"
+
+void* Allocator::get(size_t bytes, cudaStream_t st) {
+  if (alloc) return alloc(bytes, (void*)st, user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void Allocator::put(void* p, cudaStream_t st) {
+  if (!p) return;
+  if (alloc) {
+    if (free) free(p, (void*)st, user);
+  } else {
+    cudaFree(p);
+  }
+}
+
+static bool is_fin(double v) { return std::isfinite(v); }
+
+// Cholesky-Banachiewicz of the d x d correlation (C = L L^*, Section 5.2)
+static bool cholesky_host(int d, const double* C, double* L) {
+  for (int i = 0; i < d * d; ++i) L[i] = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = C[i * d + j];
+      for (int q = 0; q < j; ++q) s -= L[i * d + q] * L[j * d + q];
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        L[i * d + i] = std::sqrt(s);
+      } else {
+        L[i * d + j] = s / L[j * d + j];
+      }
+    }
+  return true;
+}
+
+int bsde_set_model_impl(ModelHost& m, const bsde_sigma* sg, double r, const bsde_payoff* pf,
+                        const bsde_penalty* pen, std::string& err) {
+  if (!sg || !pf || !pen) {
+    err = "set_model: NULL argument";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  const int d = sg->d;
+  if (d < 1 || d > BSDE_MAX_D) {
+    err = "set_model: d out of range";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  if (sg->kind < 0 || sg->kind > 3 || (pf->kind != 0 && pf->kind != 1) ||
+      (pen->obstacle != 0 && pen->obstacle != 1)) {
+    err = "set_model: unknown volatility, payoff or obstacle kind";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  if (!pf->S0) {
+    err = "set_model: payoff.S0 is required";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  ModelHost t;
+  memset(&t, 0, sizeof(t));  // padding too: models are compared bytewise
+  t.d = d;
+  t.vol_kind = sg->kind;
+  t.payoff = pf->kind;
+  t.obstacle = pen->obstacle;
+  t.T = pf->T;
+  t.r = r;
+  t.lambda = pen->lambda;
+  t.K = pf->K;
+  t.b = sg->b;
+  t.s_dupire = sg->s_dupire;
+  bool ok = is_fin(t.T) && t.T > 0 && is_fin(r) && is_fin(t.lambda) && t.lambda >= 0 &&
+            is_fin(t.K) && is_fin(t.b) && is_fin(t.s_dupire);
+  for (int j = 0; j < d; ++j) {
+    t.a[j] = sg->a ? sg->a[j] : sg->a_scalar;
+    t.kappa[j] = sg->kappa ? sg->kappa[j] : sg->kappa_scalar;
+    t.div[j] = sg->div ? sg->div[j] : 0.0;
+    t.w[j] = pf->weights ? pf->weights[j] : 1.0 / d;
+    t.S0[j] = pf->S0[j];
+    ok = ok && is_fin(t.a[j]) && is_fin(t.kappa[j]) && is_fin(t.div[j]) && is_fin(t.w[j]) &&
+         is_fin(t.S0[j]) && t.S0[j] > 0;
+  }
+  if (!ok) {
+    err = "set_model: a parameter is not finite or out of range";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      t.C[i * d + j] = sg->corr ? sg->corr[i * d + j] : (i == j ? 1.0 : sg->rho);
+  if (!cholesky_host(d, t.C, t.L)) {
+    err = "set_model: correlation matrix is not positive definite";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  m = t;
+  return BSDE_OK;
+}
+
+int bsde_set_grid_impl(GridHost& g, int d, int n, const double* lo, const double* hi, int resample,
+                       std::string& err) {
+  if (n < 1 || !lo || !hi) {
+    err = "set_grid: n < 1 or NULL box";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  GridHost t;
+  memset(&t, 0, sizeof(t));
+  t.n = n;
+  t.resample = resample ? 1 : 0;
+  for (int v = 0; v <= d; ++v) {
+    if (!(is_fin(lo[v]) && is_fin(hi[v]) && hi[v] > lo[v])) {
+      err = "set_grid: box needs finite lo < hi in every variate";
+      return BSDE_ERR_INVALID_ARG;
+    }
+    t.lo[v] = lo[v];
+    t.hi[v] = hi[v];
+  }
+  g = t;
+  return BSDE_OK;
+}
+
+Problem::~Problem() {
+  destroy_graph();
+  for (auto e : events) cudaEventDestroy(e);
+}
+
+void Problem::destroy_graph() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+  gexec = nullptr;
+  graph_key.clear();
+}
+
+void Problem::ensure_events(int count) {
+  while ((int)events.size() < count) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) break;
+    events.push_back(e);
+  }
+}
+
+// launch shape of the path kernel: threads per CTA and paths per thread,
+// limited by the shared memory of the per-thread Chebyshev tables
+int Problem::choose_launch(int d, int p, int eta, int N, int M, bool mx, int& tpb, int& ppt) {
+  tpb = mx ? 128 : 64;
+  while (tpb > 32 && paths_smem_bytes(d, p, eta, N, tpb, mx) > 220 * 1024) tpb >>= 1;
+  if (paths_smem_bytes(d, p, eta, N, tpb, mx) > 220 * 1024) return BSDE_ERR_INVALID_ARG;
+  // about 512 paths per CTA, fewer for small M
+  ppt = 4;
+  while (ppt > 1 && (long long)tpb * ppt > 2LL * M) ppt >>= 1;
+  return BSDE_OK;
+}
+
+size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int tpb, int ppt) {
+  (void)N;
+  const int n_pad = (n + 31) / 32 * 32;
+  const int p_pad = (p + 127) / 128 * 128;
+  const int chunks = (M + tpb * ppt - 1) / (tpb * ppt);
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
+  add((size_t)n * 8);
+  add((size_t)d * n * 8);
+  add((size_t)p * n_pad * 8);
+  if (mx) {
+    add((size_t)p_pad * n_pad * 4);
+    add((size_t)p_pad * n_pad * 4);
+    const int side = p_pad / 128, tiles = side * (side + 1) / 2;
+    int s = 148 / tiles;
+    if (s < 1) s = 1;
+    if (s > n_pad / 32) s = n_pad / 32;
+    add((size_t)tiles * s * 128 * 128 * 4);
+  }
+  add((size_t)n * chunks * 8);
+  add((size_t)n * 8);
+  add((size_t)p * p * 8);
+  add((size_t)p * 8 * 3);
+  add((size_t)(n > p ? n : p) * 8);
+  add((size_t)p * 8);
+  add((size_t)p * 4);
+  add((size_t)p * 8);
+  add((size_t)p);
+  add(64);
+  add((OUT_SIZE + 1 + 2 * BSDE_DMAX) * 8);
+  return b;
+}
+
+int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st) {
+  if (!has_model || !has_grid) {
+    err = "solve: set_model and set_grid must come first";
+    return BSDE_ERR_STATE;
+  }
+  const int d = model.d;
+  if (prm.M < 1 || prm.N_steps < 1 || prm.eta < 0 || prm.eta > 15 || !(prm.q > 0.0) ||
+      prm.q > 1.0 || prm.K_it < 1 || prm.K_it > BSDE_MAX_IT || prm.k_start < 0 ||
+      prm.k_start + prm.K_it >= (1 << 24)) {
+    err = "solve: parameter out of range (M, N_steps >= 1; 0 <= eta <= 15; 0 < q <= 1; "
+          "1 <= K_it <= 64)";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  if (!paths_supported_d(d)) {
+    err = "solve: the path kernel is compiled for d = 1..10";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  // basis (cached per (d, eta, q))
+  const auto nu_new = build_multi_indices(d + 1, prm.eta, prm.q);
+  if (nu_new != nus) {
+    nus = nu_new;
+    int mdeg = 0;
+    if (!pack_multi_indices(nus, pairs, nnz, mdeg)) {
+      err = "solve: basis needs more than 8 active variates or a degree above 15";
+      nus.clear();
+      return BSDE_ERR_INVALID_ARG;
+    }
+    eta_used = mdeg;
+    coeffs_valid = false;
+  }
+  const int p = (int)nus.size();
+  const int n = grid.n;
+  if (!prm.allow_underdetermined && 2 * p > n) {
+    std::ostringstream os;
+    os << "solve: basis size p = " << p << " exceeds n/2 = " << n / 2;
+    err = os.str();
+    return BSDE_ERR_ILLPOSED;
+  }
+  Shape s;
+  s.d = d;
+  s.n = n;
+  s.n_pad = (n + 31) / 32 * 32;
+  s.p = p;
+  s.p_pad = (p + 127) / 128 * 128;
+  s.eta = eta_used < 1 ? 1 : eta_used;
+  s.M = prm.M;
+  s.N = prm.N_steps;
+  s.mixed = mixed;
+  if (choose_launch(d, p, s.eta, s.N, s.M, mixed, s.tpb, s.ppt) != BSDE_OK) {
+    err = "solve: basis and step count too large for the shared-memory tables";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  s.chunks = (s.M + s.tpb * s.ppt - 1) / (s.tpb * s.ppt);
+  if (!block || !(s == alloc_shape)) {
+    const size_t need = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt);
+    if (budget && need > budget) {
+      std::ostringstream os;
+      os << "solve: needs " << need << " bytes of device memory, budget " << budget;
+      err = os.str();
+      return BSDE_ERR_NOMEM;
+    }
+    destroy_graph();
+    if (block) al.put(block, st);
+    block = nullptr;
+    block_bytes = 0;
+    void* b = al.get(need, st);
+    if (!b) {
+      err = "solve: device allocation failed";
+      return BSDE_ERR_NOMEM;
+    }
+    block = b;
+    block_bytes = need;
+    alloc_shape = s;
+    if (cudaMemsetAsync(block, 0, need, st) != cudaSuccess) {
+      err = "solve: cudaMemsetAsync failed";
+      return BSDE_ERR_CUDA;
+    }
+    char* c = (char*)block;
+    auto take = [&](size_t x) {
+      char* r = c;
+      c += (x + 255) / 256 * 256;
+      return (void*)r;
+    };
+    ProblemDev P;
+    P.n = n;
+    P.n_pad = s.n_pad;
+    P.p = p;
+    P.p_pad = s.p_pad;
+    P.eta = s.eta;
+    P.chunks = s.chunks;
+    P.t = (double*)take((size_t)n * 8);
+    P.x = (double*)take((size_t)d * n * 8);
+    P.B = (double*)take((size_t)p * s.n_pad * 8);
+    if (mixed) {
+      P.Bhi = (float*)take((size_t)s.p_pad * s.n_pad * 4);
+      P.Blo = (float*)take((size_t)s.p_pad * s.n_pad * 4);
+      const int side = s.p_pad / 128, tiles = side * (side + 1) / 2;
+      int sp = 148 / tiles;
+      if (sp < 1) sp = 1;
+      if (sp > s.n_pad / 32) sp = s.n_pad / 32;
+      P.gram_part = (float*)take((size_t)tiles * sp * 128 * 128 * 4);
+    }
+    P.partial = (double*)take((size_t)n * s.chunks * 8);
+    P.c = (double*)take((size_t)n * 8);
+    P.A = (double*)take((size_t)p * p * 8);
+    P.rhs = (double*)take((size_t)p * 8 * 3);
+    P.delta = P.rhs + p;
+    P.res = P.rhs + 2 * p;
+    P.v = (double*)take((size_t)(n > p ? n : p) * 8);  // also Cholesky scratch (p)
+    P.alpha = (double*)take((size_t)p * 8);
+    P.alpha32 = (float*)take((size_t)p * 4);
+    P.pairs = (uint2*)take((size_t)p * 8);
+    P.nnz = (uint8_t*)take((size_t)p);
+    P.key = (uint32_t*)take(64);
+    P.status = (int*)(P.key + 4);
+    P.out = (double*)take((OUT_SIZE + 1 + 2 * BSDE_DMAX) * 8);
+    dev = P;
+    coeffs_valid = false;
+  }
+  shape = s;
+  dev.chunks = s.chunks;
+  // tables, read-out point, key
+  cudaError_t e = cudaMemcpyAsync(dev.pairs, pairs.data(), (size_t)p * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dev.nnz, nnz.data(), (size_t)p, cudaMemcpyHostToDevice, st);
+  double logS0[BSDE_DMAX];
+  for (int j = 0; j < d; ++j) logS0[j] = std::log(model.S0[j]);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dev.out + OUT_SIZE + 1 + BSDE_DMAX, logS0, (size_t)d * 8,
+                        cudaMemcpyHostToDevice, st);
+  uint32_t key[2] = {(uint32_t)(prm.seed & 0xffffffffu), (uint32_t)(prm.seed >> 32)};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dev.key, key, 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev.status, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // key/logS0 live on this stack
+  if (e != cudaSuccess) {
+    err = std::string("solve: upload failed: ") + cudaGetErrorString(e);
+    return BSDE_ERR_CUDA;
+  }
+  return BSDE_OK;
+}
+
+int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t st,
+                               cudaEvent_t* ev) {
+  const bool rec = ev != nullptr;
+  const uint32_t kp = grid.resample ? (uint32_t)k : 0u;
+  launch_points(model, grid, dev, kp, st);
+  launch_basis(model, grid, dev, mixed, st);
+  if (rec) cudaEventRecord(ev[0], st);
+  cudaError_t e = launch_paths(model, grid, dev, shape.M, shape.N, (uint32_t)k, mixed, shape.tpb,
+                               shape.ppt, st);
+  if (e != cudaSuccess) {
+    err = std::string("path kernel launch failed: ") + cudaGetErrorString(e);
+    return BSDE_ERR_CUDA;
+  }
+  if (rec) cudaEventRecord(ev[1], st);
+  launch_reduce_c(dev, shape.M, st);
+  if (rec) cudaEventRecord(ev[2], st);
+  if (mixed) {
+    e = launch_gram_tc(dev, st);
+    if (e != cudaSuccess) {
+      err = std::string("tensor-core Gram launch failed: ") + cudaGetErrorString(e);
+      return BSDE_ERR_CUDA;
+    }
+  } else {
+    launch_gram_f64(dev, st);
+  }
+  if (rec) cudaEventRecord(ev[3], st);
+  launch_rhs(dev, st);
+  if (rec) cudaEventRecord(ev[4], st);
+  launch_cholesky(dev, st);
+  launch_chol_solve(dev, dev.rhs, dev.delta, st);
+  const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 0);
+  for (int r = 0; r < refine; ++r) {
+    launch_refine_residual(dev, st);
+    launch_chol_solve(dev, dev.res, dev.delta, st);
+  }
+  if (rec) cudaEventRecord(ev[5], st);
+  launch_update(dev, k - prm.k_start, st);
+  launch_eval_x0(model, grid, dev, k - prm.k_start, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("kernel launch failed: ") + cudaGetErrorString(e);
+    return BSDE_ERR_CUDA;
+  }
+  return BSDE_OK;
+}
+
+int Problem::enqueue_solve(const bsde_solve_params& prm, cudaStream_t st) {
+  const int nev = prm.timing ? 6 * prm.K_it : 0;
+  if (nev) ensure_events(nev);
+  for (int it = 0; it < prm.K_it; ++it) {
+    const int rc = enqueue_iteration(prm, prm.k_start + it, st,
+                                     nev && (int)events.size() >= nev ? &events[6 * it] : nullptr);
+    if (rc != BSDE_OK) return rc;
+  }
+  return BSDE_OK;
+}
+
+int Problem::start(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st,
+                   cudaEvent_t e0, cudaEvent_t e1) {
+  int rc = prepare(prm, al, budget, st);
+  if (rc != BSDE_OK) return rc;
+  if (prm.k_start == 0) {
+    if (cudaMemsetAsync(dev.alpha, 0, (size_t)shape.p * 8, st) != cudaSuccess ||
+        cudaMemsetAsync(dev.alpha32, 0, (size_t)shape.p * 4, st) != cudaSuccess) {
+      err = "solve: reset of the coefficients failed";
+      return BSDE_ERR_CUDA;
+    }
+  } else if (!coeffs_valid) {
+    err = "solve: k_start > 0 needs coefficients from bsde_set_coeffs or an earlier solve";
+    return BSDE_ERR_STATE;
+  }
+  cudaMemsetAsync(dev.out + OUT_PRICE_IT, 0, 3 * 64 * 8, st);
+  if (prm.use_graph) {
+    std::ostringstream os;
+    os << shape.d << ' ' << shape.n << ' ' << shape.p << ' ' << shape.M << ' ' << shape.N << ' '
+       << prm.K_it << ' ' << prm.k_start << ' ' << prm.refine_steps << ' ' << prm.timing << ' '
+       << mixed << ' ' << (void*)block;
+    if (!gexec || os.str() != graph_key) {
+      destroy_graph();
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        err = std::string("solve: stream capture failed: ") + cudaGetErrorString(e);
+        return BSDE_ERR_CUDA;
+      }
+      rc = enqueue_solve(prm, st);
+      e = cudaStreamEndCapture(st, &graph);
+      if (rc == BSDE_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (rc != BSDE_OK || e != cudaSuccess) {
+        if (rc == BSDE_OK) err = std::string("solve: graph capture failed: ") + cudaGetErrorString(e);
+        gexec = nullptr;
+        cudaGetLastError();
+        return rc != BSDE_OK ? rc : BSDE_ERR_CUDA;
+      }
+      graph_key = os.str();
+    }
+    cudaEventRecord(e0, st);
+    cudaError_t e = cudaGraphLaunch(gexec, st);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess) {
+      err = std::string("solve: graph launch failed: ") + cudaGetErrorString(e);
+      return BSDE_ERR_CUDA;
+    }
+  } else {
+    cudaEventRecord(e0, st);
+    rc = enqueue_solve(prm, st);
+    cudaEventRecord(e1, st);
+    if (rc != BSDE_OK) return rc;
+  }
+  return BSDE_OK;
+}
+
+int Problem::complete(const bsde_solve_params& prm, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                      bsde_report* rep) {
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e != cudaSuccess) {
+    err = std::string("solve: device error: ") + cudaGetErrorString(e);
+    return BSDE_ERR_CUDA;
+  }
+  coeffs_valid = true;
+  return finish_report(prm, st, rep, ms);
+}
+
+int Problem::solve(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st,
+                   bsde_report* rep) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return BSDE_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return BSDE_ERR_CUDA;
+  }
+  int rc = start(prm, al, budget, st, e0, e1);
+  if (rc == BSDE_OK) rc = complete(prm, st, e0, e1, rep);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int Problem::finish_report(const bsde_solve_params& prm, cudaStream_t st, bsde_report* rep,
+                           float ms_total) {
+  std::vector<double> out(OUT_SIZE);
+  int status = 0;
+  cudaError_t e = cudaMemcpyAsync(out.data(), dev.out, OUT_SIZE * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, dev.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    err = std::string("solve: report copy failed: ") + cudaGetErrorString(e);
+    return BSDE_ERR_CUDA;
+  }
+  int rc = BSDE_OK;
+  if (status & ST_NOT_PD) {
+    err = "solve: the Gram matrix is not positive definite (Cholesky pivot <= 0)";
+    rc = BSDE_ERR_NOT_PD;
+  } else if (status & ST_TIMEOUT) {
+    err = "solve: a bounded device wait gave up";
+    rc = BSDE_ERR_TIMEOUT;
+  }
+  if (rep) {
+    bsde_report r;
+    memset(&r, 0, sizeof(r));
+    r.status = rc;
+    r.d = model.d;
+    r.p = shape.p;
+    r.K_it = prm.K_it;
+    r.price = out[OUT_PRICE];
+    for (int j = 0; j < model.d; ++j) {
+      r.dudx[j] = out[OUT_DUDX + j];
+      r.delta[j] = out[OUT_DUDX + j] / model.S0[j];
+    }
+    for (int k = 0; k < prm.K_it && k < BSDE_MAX_IT; ++k) {
+      r.price_iter[k] = out[OUT_PRICE_IT + k];
+      r.resid_l2[k] = out[OUT_RES2 + k];
+      r.resid_linf[k] = out[OUT_RESI + k];
+    }
+    r.ms_total = ms_total;
+    r.path_steps = (double)prm.K_it * shape.n * (double)shape.M * shape.N;
+    r.path_steps_per_s = ms_total > 0 ? r.path_steps / (ms_total * 1e-3) : 0.0;
+    r.path_launches = prm.K_it;
+    const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 0);
+    const int panels = (shape.p + 31) / 32;
+    const int chol = 1 + 3 * panels - 2;
+    r.kernel_launches =
+        prm.K_it * (2 + 1 + 1 + (mixed ? 2 : 1) + 1 + chol + 1 + refine * 3 + 1 + 3);
+    // points, basis, paths, reduce, Gram (+ reduce), rhs, Cholesky, solve,
+    // refinement (2 GEMVs + solve each), update, read-out (3)
+    if (prm.timing && (int)events.size() >= 6 * prm.K_it) {
+      double mp = 0, mg = 0, msv = 0;
+      for (int k = 0; k < prm.K_it; ++k) {
+        float a = 0, b = 0, c = 0;
+        if (cudaEventElapsedTime(&a, events[6 * k], events[6 * k + 1]) == cudaSuccess) mp += a;
+        if (cudaEventElapsedTime(&b, events[6 * k + 2], events[6 * k + 3]) == cudaSuccess) mg += b;
+        if (cudaEventElapsedTime(&c, events[6 * k + 4], events[6 * k + 5]) == cudaSuccess) msv += c;
+      }
+      cudaGetLastError();
+      r.ms_paths = mp;
+      r.ms_gram = mg;
+      r.ms_solve = msv;
+    }
+    *rep = r;
+  }
+  return rc;
+}
+
+void Problem::release(Allocator& al, cudaStream_t st) {
+  destroy_graph();
+  if (block) al.put(block, st);
+  block = nullptr;
+  block_bytes = 0;
+  alloc_shape = Shape();
+  coeffs_valid = false;
+}

@@ -1,0 +1,83 @@
+// runtime.h -- host runtime of one resident BSDE problem: device memory
+// (one arena from the caller's allocator), the per-iteration launch sequence
+// of Algorithm 2 and the captured CUDA graph of a whole solve.  Used by the
+// C ABI (api.cu) and by the serving loop (server.cu).
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bsde.h"
+#include "common.cuh"
+
+struct Allocator {
+  bsde_alloc_fn alloc = nullptr;
+  bsde_free_fn free = nullptr;
+  void* user = nullptr;
+  void* get(size_t bytes, cudaStream_t st);
+  void put(void* p, cudaStream_t st);
+};
+
+struct Shape {
+  int d = 0, n = 0, n_pad = 0, p = 0, p_pad = 0, eta = 0, M = 0, N = 0;
+  int chunks = 0, tpb = 0, ppt = 0, splits = 0;
+  bool mixed = false;
+  bool operator==(const Shape& o) const {
+    return d == o.d && n == o.n && p == o.p && eta == o.eta && M == o.M && N == o.N &&
+           tpb == o.tpb && ppt == o.ppt && mixed == o.mixed;
+  }
+};
+
+class Problem {
+ public:
+  ModelHost model;
+  GridHost grid;
+  bool has_model = false, has_grid = false, coeffs_valid = false;
+  bool mixed = true;
+  Shape shape;
+  ProblemDev dev;
+  std::vector<uint32_t> pairs;
+  std::vector<uint8_t> nnz;
+  std::vector<std::vector<int>> nus;
+  int eta_used = 0;  // largest single-variate degree present
+  std::string err;
+
+  ~Problem();
+  // validate params, build the basis, (re)allocate device memory; BSDE_OK or an error
+  int prepare(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st);
+  // launch one iteration k -> k+1 (no synchronisation)
+  int enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t st, cudaEvent_t* ev);
+  // full solve: alpha reset (k_start == 0), K_it iterations, report
+  int solve(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st,
+            bsde_report* rep);
+  int enqueue_solve(const bsde_solve_params& prm, cudaStream_t st);  // after prepare
+  // asynchronous halves of solve(): start() enqueues (graph or launches)
+  // between events e0 and e1; complete() waits for e1 and builds the report
+  int start(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st,
+            cudaEvent_t e0, cudaEvent_t e1);
+  int complete(const bsde_solve_params& prm, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+               bsde_report* rep);
+  int finish_report(const bsde_solve_params& prm, cudaStream_t st, bsde_report* rep,
+                    float ms_total);
+  void release(Allocator& al, cudaStream_t st);
+  void destroy_graph();  // after a model or grid change
+  size_t bytes() const { return block_bytes; }
+  static size_t estimate_bytes(int d, int n, int p, int M, int N, bool mixed, int tpb, int ppt);
+
+ private:
+  void* block = nullptr;
+  size_t block_bytes = 0;
+  Shape alloc_shape;
+  // graph of a whole solve
+  cudaGraphExec_t gexec = nullptr;
+  std::string graph_key;
+  std::vector<cudaEvent_t> events;  // 6 per iteration when timing
+  int choose_launch(int d, int p, int eta, int N, int M, bool mixed, int& tpb, int& ppt);
+  void ensure_events(int count);
+};
+
+int bsde_set_model_impl(ModelHost& m, const bsde_sigma* sigma, double r, const bsde_payoff* payoff,
+                        const bsde_penalty* penalty, std::string& err);
+int bsde_set_grid_impl(GridHost& g, int d, int n, const double* lo, const double* hi,
+                       int resample, std::string& err);

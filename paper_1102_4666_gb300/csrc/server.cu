@@ -1,0 +1,291 @@
+// server.cu -- continuous-batching serving loop for pricing / hedging
+// requests (bsde_server_* of include/bsde.h).
+//
+// A worker thread admits queued requests while slots and the device-memory
+// budget allow.  Each admitted request gets a resident Problem (its points,
+// basis matrix, Gram matrix, coefficients and Philox key stay on the device
+// for all its Picard iterations) and a stream of its own; its whole solve is
+// one captured CUDA graph, so the iterations of all admitted requests run
+// concurrently on the GPU.  When a request's completion event fires, the
+// worker builds its report, records its latency (submit -> completion),
+// frees its memory and admits the next request in the queue.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "runtime.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() {
+  return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+  uint64_t id = 0;
+  ModelHost model;
+  GridHost grid;
+  bsde_solve_params prm;
+  double t_submit = 0.0, t_done = 0.0;
+  size_t bytes = 0;
+  std::unique_ptr<Problem> prob;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bsde_report rep;
+  int rc = 0;
+};
+
+}  // namespace
+
+struct bsde_server {
+  bsde_server_opts opts;
+  Allocator al;
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  std::thread worker;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::deque<std::unique_ptr<Req>> queue;
+  std::vector<std::unique_ptr<Req>> running;
+  std::map<uint64_t, std::unique_ptr<Req>> done;
+  std::vector<cudaStream_t> free_streams;
+  size_t used_bytes = 0;
+  std::vector<double> latencies_ms;
+  double path_steps = 0.0, busy_s = 0.0, busy_since = -1.0;
+  uint64_t completed = 0;
+  std::string err;
+
+  void loop();
+  bool admit_one(std::unique_lock<std::mutex>& lk);
+};
+
+bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
+  if (queue.empty() || (int)running.size() >= opts.max_slots) return false;
+  Req* r = queue.front().get();
+  if (opts.mem_budget && used_bytes + r->bytes > opts.mem_budget && !running.empty()) return false;
+  std::unique_ptr<Req> req = std::move(queue.front());
+  queue.pop_front();
+  used_bytes += req->bytes;
+  if (busy_since < 0) busy_since = now_s();
+  cudaStream_t st;
+  if (!free_streams.empty()) {
+    st = free_streams.back();
+    free_streams.pop_back();
+  } else {
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  }
+  req->stream = st;
+  lk.unlock();
+  // device work outside the lock: allocation, capture, graph launch
+  req->prob.reset(new Problem());
+  Problem& P = *req->prob;
+  P.mixed = (opts.precision == BSDE_PREC_MIXED);
+  P.model = req->model;
+  P.grid = req->grid;
+  P.has_model = P.has_grid = true;
+  cudaEventCreate(&req->e0);
+  cudaEventCreate(&req->e1);
+  req->rc = P.start(req->prm, al, 0, st, req->e0, req->e1);
+  lk.lock();
+  if (req->rc != BSDE_OK) {
+    // failed before reaching the device: complete immediately
+    memset(&req->rep, 0, sizeof(req->rep));
+    req->rep.status = req->rc;
+    req->t_done = now_s();
+    P.release(al, st);
+    used_bytes -= req->bytes;
+    free_streams.push_back(st);
+    done[req->id] = std::move(req);
+    cv_done.notify_all();
+    return true;
+  }
+  running.push_back(std::move(req));
+  return true;
+}
+
+void bsde_server::loop() {
+  cudaSetDevice(opts.device);
+  std::unique_lock<std::mutex> lk(mu);
+  while (!stop) {
+    while (admit_one(lk)) {
+    }
+    // completions
+    bool progressed = false;
+    for (size_t i = 0; i < running.size();) {
+      Req* r = running[i].get();
+      if (cudaEventQuery(r->e1) == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      lk.unlock();
+      r->rc = r->prob->complete(r->prm, r->stream, r->e0, r->e1, &r->rep);
+      r->rep.status = r->rc;
+      r->t_done = now_s();
+      r->prob->release(al, r->stream);
+      cudaStreamSynchronize(r->stream);
+      cudaEventDestroy(r->e0);
+      cudaEventDestroy(r->e1);
+      r->e0 = r->e1 = nullptr;
+      lk.lock();
+      used_bytes -= r->bytes;
+      free_streams.push_back(r->stream);
+      latencies_ms.push_back((r->t_done - r->t_submit) * 1e3);
+      if (r->rc == BSDE_OK) path_steps += r->rep.path_steps;
+      ++completed;
+      r->prob.reset();
+      done[r->id] = std::move(running[i]);
+      running.erase(running.begin() + i);
+      progressed = true;
+      cv_done.notify_all();
+    }
+    if (running.empty() && busy_since >= 0) {
+      busy_s += now_s() - busy_since;
+      busy_since = -1.0;
+    }
+    if (!progressed) {
+      if (running.empty() && queue.empty())
+        cv.wait(lk);
+      else
+        cv.wait_for(lk, std::chrono::microseconds(200));
+    }
+  }
+}
+
+extern "C" {
+
+int bsde_server_create(bsde_server** out, const bsde_server_opts* o) {
+  if (!out || !o || o->max_slots < 1 || o->max_slots > 64 ||
+      (o->precision != BSDE_PREC_FP64 && o->precision != BSDE_PREC_MIXED))
+    return BSDE_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || o->device < 0 || o->device >= ndev) {
+    cudaGetLastError();
+    return BSDE_ERR_CUDA;
+  }
+  try {
+    bsde_server* s = new bsde_server();
+    s->opts = *o;
+    s->worker = std::thread([s] { s->loop(); });
+    *out = s;
+    return BSDE_OK;
+  } catch (...) {
+    return BSDE_ERR_NOMEM;
+  }
+}
+
+int bsde_server_submit(bsde_server* s, const bsde_request* rq, uint64_t* id) {
+  if (!s || !rq || !id) return BSDE_ERR_INVALID_ARG;
+  try {
+    std::unique_ptr<Req> r(new Req());
+    std::string e;
+    int rc = bsde_set_model_impl(r->model, &rq->sigma, rq->r, &rq->payoff, &rq->penalty, e);
+    if (rc == BSDE_OK)
+      rc = bsde_set_grid_impl(r->grid, r->model.d, rq->n, rq->lo, rq->hi, 1, e);
+    if (rc != BSDE_OK) {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->err = e;
+      return rc;
+    }
+    r->prm = rq->params;
+    int p = 0;
+    rc = bsde_basis_size(r->model.d, r->prm.eta, r->prm.q, &p);
+    if (rc != BSDE_OK) return rc;
+    const int tpb = s->opts.precision == BSDE_PREC_MIXED ? 128 : 64;
+    r->bytes = Problem::estimate_bytes(r->model.d, rq->n, p, r->prm.M, r->prm.N_steps,
+                                       s->opts.precision == BSDE_PREC_MIXED, tpb, 4);
+    r->t_submit = now_s();
+    std::lock_guard<std::mutex> g(s->mu);
+    if (s->opts.mem_budget && r->bytes > s->opts.mem_budget) {
+      s->err = "submit: request larger than the server's memory budget";
+      return BSDE_ERR_NOMEM;
+    }
+    r->id = s->next_id++;
+    *id = r->id;
+    s->queue.push_back(std::move(r));
+    s->cv.notify_all();
+    return BSDE_OK;
+  } catch (...) {
+    return BSDE_ERR_NOMEM;
+  }
+}
+
+int bsde_server_poll(bsde_server* s, uint64_t id, bsde_report* rep) {
+  if (!s) return BSDE_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->done.find(id);
+  if (it == s->done.end()) {
+    for (auto& r : s->queue)
+      if (r->id == id) return 0;
+    for (auto& r : s->running)
+      if (r->id == id) return 0;
+    s->err = "poll: unknown request id";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  if (rep) *rep = it->second->rep;
+  s->done.erase(it);
+  return 1;
+}
+
+int bsde_server_drain(bsde_server* s, double timeout_ms) {
+  if (!s) return BSDE_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto pred = [s] { return s->queue.empty() && s->running.empty(); };
+  if (timeout_ms > 0) {
+    if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred))
+      return BSDE_ERR_TIMEOUT;
+  } else {
+    s->cv_done.wait(lk, pred);
+  }
+  return BSDE_OK;
+}
+
+int bsde_server_stats_get(bsde_server* s, bsde_server_stats* st) {
+  if (!s || !st) return BSDE_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  memset(st, 0, sizeof(*st));
+  st->completed = s->completed;
+  st->queued = s->queue.size();
+  st->running = s->running.size();
+  std::vector<double> l = s->latencies_ms;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double q) {
+    if (l.empty()) return 0.0;
+    size_t idx = (size_t)(q * (double)(l.size() - 1) + 0.5);
+    return l[std::min(idx, l.size() - 1)];
+  };
+  st->p50_ms = pct(0.50);
+  st->p99_ms = pct(0.99);
+  st->path_steps = s->path_steps;
+  double busy = s->busy_s + (s->busy_since >= 0 ? now_s() - s->busy_since : 0.0);
+  st->busy_s = busy;
+  st->path_steps_per_s = busy > 0 ? s->path_steps / busy : 0.0;
+  return BSDE_OK;
+}
+
+void bsde_server_destroy(bsde_server* s) {
+  if (!s) return;
+  bsde_server_drain(s, 0);
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  s->worker.join();
+  cudaSetDevice(s->opts.device);
+  for (auto st : s->free_streams) cudaStreamDestroy(st);
+  delete s;
+}
+
+const char* bsde_server_last_error(const bsde_server* s) { return s ? s->err.c_str() : ""; }
+
+}  // extern "C"

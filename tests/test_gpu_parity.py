@@ -1,0 +1,294 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+the same seeded inputs and the same Philox counters.
+
+Tolerances:
+  * points: bit-exact (both sides round the same IEEE operations);
+  * FP64 mode: 1e-9 relative on coefficients and corrections, where the two
+    sides differ only by libm ulps and summation order;
+  * mixed mode: 1e-4 relative on price and delta; the corrections c_i agree
+    to a tolerance derived from FP32 rounding along the path (see
+    MIXED_C_TOL below).
+For the penalised (American) configurations the Picard map amplifies a
+perturbation by up to lambda (T - t) per iteration, so those are compared
+one iteration at a time from the same alpha^k ("teacher forcing").
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import bsde_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+NTH = os.cpu_count() or 1
+# FP32 relative rounding u = 2^-24; a path of N steps accumulates about
+# sqrt(N) u relative error in X, the Box-Muller/exp/tanh approximations add a
+# few 1e-7; the evaluation of u^k sums p terms of size |alpha_l| (error about
+# p u max|alpha|).  The mean over M paths averages the random part.  A bound
+# of 2e-5 times the scale of the integrand (max of |Phi|, |u|, T |g1|) covers
+# all the configurations below with margin.
+MIXED_C_TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def G():
+    import paper_1102_4666_gb300 as G
+    return G
+
+
+def solver(G, cfg, prec):
+    return G.Solver(cfg, precision=prec)
+
+
+def rel(a, b):
+    return np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(1e-300, np.max(np.abs(np.asarray(b))))
+
+
+# ---------------------------------------------------------------------------
+# points and basis
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_points_bit_exact(G, prec):
+    cfg = workloads.config("c3", n=1000, M=8, N=2, eta=2)
+    s = solver(G, cfg, prec)
+    nu = O.multi_index_set(6, 2)
+    t, x, c, a1 = s.iterate(3, np.zeros(len(nu)))
+    s.close()
+    to, xo = O.points(cfg, 3)
+    assert np.array_equal(t, to)
+    assert np.array_equal(x, xo)
+
+
+# ---------------------------------------------------------------------------
+# config 1 (European put d=1): whole solve
+# ---------------------------------------------------------------------------
+
+def test_c1_fp64_full_trajectory(G):
+    cfg = workloads.config("c1")
+    s = solver(G, cfg, "fp64")
+    rep = s.solve(use_graph=1)
+    alpha = s.coeffs()
+    s.close()
+    ref = O.solve(cfg, nthreads=NTH)
+    assert rel(alpha, ref["alpha"]) < 1e-9
+    assert abs(rep.price - ref["price"]) < 1e-9 * abs(ref["price"])
+    assert abs(rep.delta[0] - ref["delta"][0]) < 1e-9 * abs(ref["delta"][0])
+    for k, h in enumerate(ref["history"]):
+        assert abs(rep.price_iter[k] - h["price"]) < 1e-9 * abs(h["price"])
+
+
+def test_c1_mixed_price_delta(G):
+    cfg = workloads.config("c1")
+    s = solver(G, cfg, "mixed")
+    rep = s.solve(use_graph=1)
+    s.close()
+    ref = O.solve(cfg, nthreads=NTH)
+    assert abs(rep.price - ref["price"]) <= 1e-4 * abs(ref["price"])
+    assert abs(rep.delta[0] - ref["delta"][0]) <= 1e-4 * abs(ref["delta"][0])
+
+
+# ---------------------------------------------------------------------------
+# one iteration from the same alpha^k (teacher forcing)
+# ---------------------------------------------------------------------------
+
+CASES = {
+    # name: (config, overrides)
+    "c2_small": ("c2", dict(n=300, M=400, N=50, eta=6)),
+    "c3_small": ("c3", dict(n=480, M=200, N=25, eta=4)),
+    "c4_small": ("c4", dict(n=800, M=128, N=20, eta=3)),
+    "d2_ragged": ("c3", dict(d=2, n=70, M=77, N=7, eta=3)),
+    "d3_call": ("c3", dict(d=3, n=90, M=130, N=9, eta=3, payoff="call")),
+    "d10_tail": ("c4", dict(n=200, M=33, N=7, eta=2)),
+    "d1_raw_obstacle": ("c2", dict(n=120, M=200, N=13, eta=5, obstacle="raw")),
+}
+
+
+def _case(name):
+    base, over = CASES[name]
+    cfg = workloads.config(base)
+    d = over.get("d", cfg["d"])
+    if d != cfg["d"]:
+        cfg = workloads.make(d=d, T=cfg["T"], r=cfg["r"], K=cfg["K"], S0=100.0, vol=cfg["vol"],
+                             rho=cfg["rho"], lam=cfg["lambda"], n=cfg["n"], M=cfg["M"], N=cfg["N"],
+                             eta=cfg["eta"], K_it=1, seed=cfg["seed"])
+    for k, v in over.items():
+        if k != "d":
+            cfg[k] = v
+    return cfg
+
+
+def _alpha(cfg, nu, scale=2.0, seed=3):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(len(nu)) * scale / np.sqrt(1 + nu.sum(axis=1)) ** 2
+    a[0] += 5.0
+    return a
+
+
+def _scale(cfg, nu, alpha, t, x):
+    u = O.basis_matrix(cfg, nu, t, x) @ alpha
+    return max(1.0, cfg["K"] * 0.5, np.max(np.abs(u)) * (1.0 + cfg["lambda"] * cfg["T"]))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_teacher_forced_iteration_fp64(G, name):
+    cfg = _case(name)
+    nu = O.multi_index_set(cfg["d"] + 1, cfg["eta"])
+    a0 = _alpha(cfg, nu)
+    s = solver(G, cfg, "fp64")
+    t, x, c, a1 = s.iterate(2, a0)
+    s.close()
+    it = O.iteration(cfg, nu, a0, 2, nthreads=NTH)
+    sc = _scale(cfg, nu, a0, t, x)
+    assert np.max(np.abs(c - it["c"])) < 1e-9 * sc
+    assert rel(a1 - a0, it["alpha"] - a0) < 1e-8
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_teacher_forced_iteration_mixed(G, name):
+    cfg = _case(name)
+    nu = O.multi_index_set(cfg["d"] + 1, cfg["eta"])
+    a0 = _alpha(cfg, nu)
+    s = solver(G, cfg, "mixed")
+    t, x, c, a1 = s.iterate(2, a0)
+    s.close()
+    it = O.iteration(cfg, nu, a0, 2, nthreads=NTH)
+    sc = _scale(cfg, nu, a0, t, x)
+    assert np.max(np.abs(c - it["c"])) < MIXED_C_TOL * sc
+    # price and delta of alpha^{k+1}
+    pg, dg = O.price_delta(cfg, nu, a1)
+    po, do = O.price_delta(cfg, nu, it["alpha"])
+    assert abs(pg - po) <= 1e-4 * max(abs(po), 1.0)
+    assert np.max(np.abs(dg - do)) <= 1e-4 * max(np.max(np.abs(do)), 1e-2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_refit_solves_the_normal_equations(G, prec):
+    """alpha^{k+1} - alpha^k is the least-squares fit of the GPU's own c on
+    the (bit-exact) points: isolates the Gram matrix (tensor cores in mixed
+    mode), the Cholesky solve and the refinement."""
+    cfg = workloads.config("c4", n=900, M=64, N=4, eta=3)
+    nu = O.multi_index_set(11, 3)
+    a0 = _alpha(cfg, nu)
+    s = solver(G, cfg, prec)
+    t, x, c, a1 = s.iterate(1, a0)
+    s.close()
+    B = O.basis_matrix(cfg, nu, t, x)
+    delta = O.fit(B, c)
+    assert rel(a1 - a0, delta) < 1e-9
+
+
+def test_full_size_c4_sampled_points(G):
+    """c4 at its full size (n=4000, M=4000, N=100, p=364), one mixed
+    iteration in the bench's launch configuration; the oracle recomputes
+    c_i at a sample of points."""
+    cfg = workloads.config("c4")
+    nu = O.multi_index_set(11, 3)
+    a0 = _alpha(cfg, nu, scale=1.0)
+    s = solver(G, cfg, "mixed")
+    t, x, c, a1 = s.iterate(5, a0)
+    s.close()
+    idx = np.arange(0, 4000, 500)
+    co = O.correction(cfg, nu, a0, 5, idx, t[idx], x[:, idx], nthreads=NTH)
+    sc = _scale(cfg, nu, a0, t, x)
+    assert np.max(np.abs(c[idx] - co)) < MIXED_C_TOL * sc
+    # the refit at full size: normal equations of the GPU's own c
+    B = O.basis_matrix(cfg, nu, t, x)
+    assert rel(a1 - a0, O.fit(B, c)) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# vol families, outputs, determinism, errors
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["const", "abs_tanh", "sin_tanh", "dupire"])
+def test_vol_families_fp64(G, kind):
+    cfg = workloads.config("c3", n=80, M=96, N=9, eta=2)
+    if kind == "const":
+        cfg["vol"] = {"kind": "const", "a": [0.15, 0.2, 0.25, 0.3, 0.35]}
+    elif kind == "abs_tanh":
+        cfg["vol"] = {"kind": "abs_tanh", "a": 0.15, "b": 0.1, "kappa": math.log(100.0)}
+    elif kind == "dupire":
+        cfg["vol"] = {"kind": "dupire", "s": 100.0}
+    cfg["div"] = [0.0, 0.01, 0.02, 0.03, 0.1]
+    nu = O.multi_index_set(6, 2)
+    a0 = _alpha(cfg, nu)
+    s = solver(G, cfg, "fp64")
+    t, x, c, a1 = s.iterate(0, a0)
+    s.close()
+    it = O.iteration(cfg, nu, a0, 0, nthreads=NTH)
+    assert np.max(np.abs(c - it["c"])) < 1e-9 * _scale(cfg, nu, a0, t, x)
+
+
+def test_eval_price_delta_matches_oracle(G):
+    cfg = workloads.config("c3", n=400, M=64, N=5, eta=3, K_it=2)
+    s = solver(G, cfg, "fp64")
+    s.solve(use_graph=0)
+    alpha = s.coeffs()
+    rng = np.random.default_rng(8)
+    q = 17
+    tq = rng.uniform(0, 1, q)
+    S = 100.0 * np.exp(rng.uniform(-0.5, 0.5, (q, 5)))
+    price, delta = s.eval(tq, S)
+    s.close()
+    nu = O.multi_index_set(6, 3)
+    u, g = O.eval_u(cfg, nu, alpha, tq, np.log(S).T)
+    assert np.allclose(price, u, rtol=1e-12, atol=1e-12)
+    assert np.allclose(delta, (g / S.T).T, rtol=1e-11, atol=1e-13)
+
+
+def test_graph_and_direct_launch_agree_and_are_deterministic(G):
+    cfg = workloads.config("c4", n=200, M=300, N=10, K_it=3, eta=2)
+    s = solver(G, cfg, "mixed")
+    r1 = s.solve(use_graph=1)
+    a1 = s.coeffs()
+    r2 = s.solve(use_graph=0)
+    a2 = s.coeffs()
+    r3 = s.solve(use_graph=1)
+    a3 = s.coeffs()
+    s.close()
+    assert np.array_equal(a1, a2) and np.array_equal(a1, a3)
+    assert r1.price == r2.price == r3.price
+
+
+def test_checkpoint_resume_reproduces_the_run(G):
+    cfg = workloads.config("c3", n=300, M=200, N=10, eta=3, K_it=4)
+    s = solver(G, cfg, "mixed")
+    s.solve()
+    full = s.coeffs()
+    s.solve(K_it=2)
+    half = s.coeffs()
+    s.close()
+    s2 = solver(G, cfg, "mixed")
+    s2.set_coeffs(half)
+    s2.solve(K_it=2, k_start=2)
+    resumed = s2.coeffs()
+    s2.close()
+    assert np.array_equal(full, resumed)
+
+
+def test_errors_are_status_codes(G):
+    cfg = workloads.config("c3", n=20, M=10, N=3, eta=4)  # p = 210 > n/2
+    s = solver(G, cfg, "fp64")
+    rep = s.solve(check=False)
+    assert rep.status == G.ERR_ILLPOSED
+    # a basis larger than the point set: singular Gram matrix, no trap
+    cfg2 = workloads.config("c3", n=40, M=16, N=3, eta=3, K_it=1)  # p = 56 > n
+    s2 = solver(G, cfg2, "fp64")
+    rep = s2.solve(check=False, allow_underdetermined=1)
+    assert rep.status == G.ERR_NOT_PD
+    s2.close()
+    # the context stays usable after the error
+    s.cfg = workloads.config("c3", n=40, M=16, N=3, eta=1, K_it=1)
+    s.set_grid(s.cfg)
+    rep = s.solve(check=False)
+    assert rep.status == G.OK
+    s.close()
+    bad = workloads.make(d=11, T=1.0, r=0.01, K=100.0, S0=100.0, vol={"kind": "const", "a": 0.2}, rho=0.0,
+                         lam=0.0, n=100, M=8, N=2, eta=1, K_it=1, seed=1)
+    s3 = solver(G, bad, "fp64")
+    assert s3.solve(check=False).status == G.ERR_INVALID_ARG
+    s3.close()
