@@ -15,8 +15,8 @@ HEADER = os.path.join(ROOT, "include", "bsde.h")
 
 @pytest.fixture(scope="module")
 def G():
-    from paper_1102_4666_gb300 import _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__._load_builder().build()
     import paper_1102_4666_gb300 as G
     return G
 
