@@ -154,6 +154,24 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(args):
+    """A small launch of the same kernels for ncu: the d = 10 workload with
+    n = 800 points and one iteration (every kernel of an iteration runs
+    once per solve)."""
+    import torch
+    import paper_1102_4666_gb300 as G
+    cfg = workloads.config(CONFIG, n=800, K_it=1)
+    s = G.Solver(cfg, precision=args.precision)
+    for _ in range(2):
+        r = s.solve(use_graph=0, timing=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "profile", "workload": cfg["name"] + " n=800 K_it=1",
+                      "precision": args.precision, "ms_paths": r.ms_paths, "ms_gram": r.ms_gram,
+                      "ms_solve": r.ms_solve, "ms_total": r.ms_total, "price": r.price}))
+    s.close()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -204,7 +222,7 @@ def run_ours(args):
     steps_per_solve = workloads.path_steps(cfg)
     value = world * args.steps * steps_per_solve / (ms * 1e-3)
     launches = sum(r.kernel_launches for r in reps)
-    path_ms = sum(r.ms_paths for r in reps) / sum(r.path_launches for r in reps)
+    path_ms = sum(r.ms_paths for r in reps) / max(1, sum(r.path_launches for r in reps))
 
     # end to end through the public API with host buffers: model, grid and
     # parameters copied from host, report (price, delta, residuals) to host
@@ -243,7 +261,7 @@ def run_ours(args):
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     launch_steps = cfg["n"] * cfg["M"] * cfg["N"]
-    achieved = FLOPS_PER_PATH_STEP * launch_steps / (path_ms * 1e-3) / 1e12
+    achieved = FLOPS_PER_PATH_STEP * launch_steps / (path_ms * 1e-3) / 1e12 if path_ms > 0 else None
     cpu = cpu_oracle_rate(cfg, budget_s=args.cpu_budget) if not args.no_cpu else None
     rep0 = reps[-1]
     line = {
@@ -255,7 +273,8 @@ def run_ours(args):
                    "eta": 3, "p": rep0.p, "K_it": cfg["K_it"], "precision": "mixed",
                    "l2": "flushed between steps (256 MB write)", "graph": True},
         "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,float,10>", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": None,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock %.0f MHz" % sm_mhz,
                      "flops_per_path_step": FLOPS_PER_PATH_STEP, "path_kernel_ms": path_ms},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -282,7 +301,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
+    if args.case == "profile":
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -329,22 +329,31 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   return BSDE_OK;
 }
 
+// event record that also works inside stream capture (an external event
+// node of the graph, so that elapsed times can be read after a replay)
+static void record(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  cudaEventRecordWithFlags(e, st,
+                           cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t st,
                                cudaEvent_t* ev) {
   const bool rec = ev != nullptr;
   const uint32_t kp = grid.resample ? (uint32_t)k : 0u;
   launch_points(model, grid, dev, kp, st);
   launch_basis(model, grid, dev, mixed, st);
-  if (rec) cudaEventRecord(ev[0], st);
+  if (rec) record(ev[0], st);
   cudaError_t e = launch_paths(model, grid, dev, shape.M, shape.N, (uint32_t)k, mixed, shape.tpb,
                                shape.ppt, st);
   if (e != cudaSuccess) {
     err = std::string("path kernel launch failed: ") + cudaGetErrorString(e);
     return BSDE_ERR_CUDA;
   }
-  if (rec) cudaEventRecord(ev[1], st);
+  if (rec) record(ev[1], st);
   launch_reduce_c(dev, shape.M, st);
-  if (rec) cudaEventRecord(ev[2], st);
+  if (rec) record(ev[2], st);
   if (mixed) {
     e = launch_gram_tc(dev, st);
     if (e != cudaSuccess) {
@@ -354,9 +363,9 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
   } else {
     launch_gram_f64(dev, st);
   }
-  if (rec) cudaEventRecord(ev[3], st);
+  if (rec) record(ev[3], st);
   launch_rhs(dev, st);
-  if (rec) cudaEventRecord(ev[4], st);
+  if (rec) record(ev[4], st);
   launch_cholesky(dev, st);
   launch_chol_solve(dev, dev.rhs, dev.delta, st);
   const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 0);
@@ -364,7 +373,7 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
     launch_refine_residual(dev, st);
     launch_chol_solve(dev, dev.res, dev.delta, st);
   }
-  if (rec) cudaEventRecord(ev[5], st);
+  if (rec) record(ev[5], st);
   launch_update(dev, k - prm.k_start, st);
   launch_eval_x0(model, grid, dev, k - prm.k_start, st);
   e = cudaGetLastError();
