@@ -68,7 +68,8 @@ class bsde_solve_params(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("N_steps", ctypes.c_int), ("eta", ctypes.c_int), ("q", ctypes.c_double),
                 ("K_it", ctypes.c_int), ("seed", ctypes.c_uint64), ("k_start", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("use_graph", ctypes.c_int), ("timing", ctypes.c_int),
-                ("allow_underdetermined", ctypes.c_int)]
+                ("allow_underdetermined", ctypes.c_int), ("eval_mode", ctypes.c_int),
+                ("paths_tpb", ctypes.c_int), ("paths_ppt", ctypes.c_int)]
 
 
 class bsde_report(ctypes.Structure):
@@ -229,13 +230,15 @@ def model_structs(cfg):
 
 
 def solve_params(cfg, seed=None, K_it=None, k_start=0, refine_steps=-1, use_graph=1, timing=0,
-                 allow_underdetermined=0):
+                 allow_underdetermined=0, eval_mode=0, paths_tpb=0, paths_ppt=0):
     p = bsde_solve_params()
     p.M, p.N_steps, p.eta, p.q = cfg["M"], cfg["N"], cfg["eta"], cfg.get("q", 1.0)
     p.K_it = cfg["K_it"] if K_it is None else K_it
     p.seed = cfg["seed"] if seed is None else seed
     p.k_start, p.refine_steps, p.use_graph, p.timing = k_start, refine_steps, use_graph, timing
     p.allow_underdetermined = allow_underdetermined
+    p.eval_mode = eval_mode
+    p.paths_tpb, p.paths_ppt = paths_tpb, paths_ppt
     return p
 
 

@@ -27,8 +27,11 @@ struct Philox {
     uint32_t a = k0, b = k1;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-      const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-      const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+      // one 32x32 -> 64-bit multiply each (wide integer multiply-add)
+      const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u;
+      const uint64_t p1 = (uint64_t)c2 * 0xCD9E8D57u;
+      const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+      const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
       const uint32_t n0 = hi1 ^ c1 ^ a;
       const uint32_t n2 = hi0 ^ c3 ^ b;
       c0 = n0;
@@ -57,7 +60,9 @@ struct Math<float> {
                                                     float& z1) {
     const float u0 = fmaf(__uint2float_rn(w0), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float u1 = fmaf(__uint2float_rn(w1), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float rad = sqrtf(fmaxf(-2.0f * __logf(u0), 0.0f));
+    // sqrt(r2) as r2 * rsqrt(r2) (r2 >= 1e-30 keeps rsqrt finite)
+    const float r2 = fmaxf(-2.0f * __logf(u0), 1e-30f);
+    const float rad = r2 * rsqrtf(r2);
     float s, c;
     // angle 2 pi u1 - pi keeps the argument in (-pi, pi]; cos/sin flip sign
     __sincosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f), &s, &c);
@@ -70,6 +75,8 @@ struct Math<float> {
     return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f);
   }
   __device__ __forceinline__ static float sqrt(float x) { return sqrtf(x); }
+  __device__ __forceinline__ static float sin(float x) { return sinf(x); }
+  __device__ __forceinline__ static float exp_acc(float x) { return expf(x); }
   __device__ __forceinline__ static float fabs(float x) { return fabsf(x); }
   __device__ __forceinline__ static float fmax(float a, float b) { return fmaxf(a, b); }
 };
@@ -89,6 +96,8 @@ struct Math<double> {
   __device__ __forceinline__ static double exp(double x) { return ::exp(x); }
   __device__ __forceinline__ static double tanh(double x) { return ::tanh(x); }
   __device__ __forceinline__ static double sqrt(double x) { return ::sqrt(x); }
+  __device__ __forceinline__ static double sin(double x) { return ::sin(x); }
+  __device__ __forceinline__ static double exp_acc(double x) { return ::exp(x); }
   __device__ __forceinline__ static double fabs(double x) { return ::fabs(x); }
   __device__ __forceinline__ static double fmax(double a, double b) { return ::fmax(a, b); }
 };
@@ -138,6 +147,14 @@ struct ProblemDev {
   uint32_t* key = nullptr;    // [2] Philox key
   int* status = nullptr;      // [1] device status bits
   double* out = nullptr;      // report block (see OUT_* offsets)
+  // dense evaluation (basis of total degree <= 3): monomial coefficients
+  bool dense = false;
+  int pm = 0;                 // number of monomials, C(d + 4, 3)
+  double* beta = nullptr;     // [pm]
+  float* beta32 = nullptr;    // [pm]
+  int* conv_row = nullptr;    // [pm + 1] CSR rows of the Chebyshev -> monomial map
+  int* conv_l = nullptr;      // basis-function index of each entry
+  double* conv_c = nullptr;   // coefficient of each entry
 };
 
 // offsets in ProblemDev::out
@@ -175,5 +192,6 @@ void launch_eval_x0(const ModelHost& m, const GridHost& g, const ProblemDev& P, 
 void launch_eval_points(const ModelHost& m, const GridHost& g, const ProblemDev& P, int q,
                         const double* t, const double* x, double* price, double* dudx,
                         cudaStream_t st);
-size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed);
+size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed, bool dense);
+void launch_cheb2mono(const ProblemDev& P, cudaStream_t st);
 int paths_supported_d(int d);

@@ -343,7 +343,25 @@ __global__ void k_copy_price(int k, int d, double* __restrict__ out) {
   if (threadIdx.x == 0 && k >= 0 && k < 64) out[OUT_PRICE_IT + k] = out[OUT_PRICE];
 }
 
+// monomial coefficients of u^k (basis of total degree <= 3): beta_m =
+// sum over the CSR row m of coef * alpha_l, in FP64, with an FP32 copy
+__global__ void k_cheb2mono(int pm, const int* __restrict__ row, const int* __restrict__ lidx,
+                            const double* __restrict__ coef, const double* __restrict__ alpha,
+                            double* __restrict__ beta, float* __restrict__ beta32) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= pm) return;
+  double s = 0.0;
+  for (int e = row[m]; e < row[m + 1]; ++e) s += coef[e] * alpha[lidx[e]];
+  beta[m] = s;
+  beta32[m] = (float)s;
+}
+
 }  // namespace
+
+void launch_cheb2mono(const ProblemDev& P, cudaStream_t st) {
+  k_cheb2mono<<<(P.pm + 127) / 128, 128, 0, st>>>(P.pm, P.conv_row, P.conv_l, P.conv_c, P.alpha,
+                                                   P.beta, P.beta32);
+}
 
 void launch_reduce_c(const ProblemDev& P, int M, cudaStream_t st) {
   k_reduce_c<<<(P.n + 255) / 256, 256, 0, st>>>(P.n, P.chunks, M, P.partial, P.c);

@@ -17,7 +17,11 @@
 // drawn after the loop through a Brownian bridge (no divergent branch in
 // the loop).  u^k and its derivatives at (tau, X_tau) and u^k(T, X_T) come
 // from per-thread Chebyshev tables in shared memory (layout [slot][thread],
-// conflict-free).  Per-path samples are accumulated in FP64; the CTA
+// conflict-free), or, when the basis has total degree <= 3 (EV = EV_DENSE3),
+// from the monomial coefficients beta of u^k (converted from the Chebyshev
+// coefficients once per iteration) by unrolled symmetric-tensor loops whose
+// indices are compile-time constants, so that u, grad u and the Hessian stay
+// in registers.  Per-path samples are accumulated in FP64; the CTA
 // reduces them by a fixed warp-shuffle tree into partial[i][chunk], so the
 // result does not depend on scheduling.
 #pragma once
@@ -26,6 +30,12 @@
 namespace paths {
 
 enum { VK_CONST = 0, VK_TANH = 1, VK_DUPIRE = 2 };
+enum { EV_TABLES = 0, EV_DENSE3 = 1 };
+
+// monomials of total degree <= 3 in dp variates: C(dp + 3, 3)
+__host__ __device__ constexpr int ncubic(int dp) { return (dp + 3) * (dp + 2) * (dp + 1) / 6; }
+// index of (a, b), a <= b, in the row-major upper triangle of a dp x dp matrix
+__host__ __device__ constexpr int sym(int dp, int a, int b) { return a * dp - a * (a - 1) / 2 + (b - a); }
 
 template <typename R, int D>
 struct Args {
@@ -38,6 +48,7 @@ struct Args {
   int N, M, n, p, eta, chunks, tpb, ppt, tab_stride;
   int payoff, obstacle, absflag, vol_sin;
   R vb;
+  R rho;  // constant correlation (dense evaluation)
   uint32_t k;
   const uint32_t* key;
   const double* pt;
@@ -141,8 +152,98 @@ __device__ __forceinline__ void term(const R* __restrict__ tb, int S, int eta, i
   }
 }
 
-template <int VK, typename R, int D>
-__global__ void __launch_bounds__(256) k_paths(const __grid_constant__ Args<R, D> a) {
+// u^k, (d_t + L^N) u^k at z (the reduced (tau, X_tau)) and u^k at zT (the
+// reduced (T, X_T)) from the monomial coefficients of total degree <= 3,
+// ordered: constant, linear (a), quadratic (a <= b), cubic (a <= b <= c),
+// each group lexicographic.  Nested Horner form
+//   u = c + sum_i z_i (g_i + sum_{j>=i} z_j (q_ij + sum_{k>=j} t_ijk z_k)),
+// evaluated on numbers carrying (value, derivative along bt, derivative and
+// second derivative along st), where bt = (d xi_0/dt, b_j d xi_j/dx_j) and
+// st = (0, sigma_j d xi_j/dx_j).  With a constant correlation rho,
+//   1/2 sum_{jl} st_j st_l C_jl d2_jl u
+//     = 1/2 [(1 - rho) sum_j st_j^2 d2_jj u + rho d2_st u],
+// and the diagonal second derivatives come from the few monomials with a
+// repeated variate.  All loop indices are compile-time constants.
+template <typename R, int D>
+__device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __restrict__ beta,
+                                            const R* z, const R* zT, const R* bt, const R* st,
+                                            R& u, R& gen, R& uT) {
+  constexpr int DP = D + 1;
+  constexpr int NQ = DP * (DP + 1) / 2;
+  const R* bg = beta + 1;
+  const R* bq = bg + DP;
+  const R* bc3 = bq + NQ;
+  // value at (T, X_T)
+  {
+    R s = beta[0];
+    int iq = 0, it = 0;
+#pragma unroll
+    for (int i = 0; i < DP; ++i) {
+      R bi = bg[i];
+#pragma unroll
+      for (int j = i; j < DP; ++j) {
+        R aij = bq[iq++];
+#pragma unroll
+        for (int k = j; k < DP; ++k) aij += bc3[it++] * zT[k];
+        bi += zT[j] * aij;
+        // keep the coefficient loads of one (i, j) group together: without
+        // this fence the scheduler hoists all of them and runs out of registers
+        asm volatile("" ::: "memory");
+      }
+      s += zT[i] * bi;
+    }
+    uT = s;
+  }
+  // value, d_bt, d_st, d2_st and the weighted Hessian diagonal at (tau, X_tau)
+  R uv = beta[0], ub = R(0), us = R(0), uss = R(0), diag = R(0);
+  int iq = 0, it = 0;
+#pragma unroll
+  for (int i = 0; i < DP; ++i) {
+    R bv = bg[i], bb = R(0), bs = R(0), bss = R(0);
+#pragma unroll
+    for (int j = i; j < DP; ++j) {
+      const R q = bq[iq++];
+      R av = q, ab = R(0), as = R(0);
+      if (i == j && i > 0) diag += R(2) * st[i] * st[i] * q;
+#pragma unroll
+      for (int k = j; k < DP; ++k) {
+        const R t = bc3[it++];
+        av += t * z[k];
+        ab += t * bt[k];
+        if (k > 0) as += t * st[k];
+        if (i == j && j < k && i > 0) diag += R(2) * st[i] * st[i] * t * z[k];
+        if (i < j && j == k && j > 0) diag += R(2) * st[j] * st[j] * t * z[i];
+        if (i == j && j == k && i > 0) diag += R(6) * st[i] * st[i] * t * z[i];
+      }
+      // (z_j, bt_j, st_j, 0) * (av, ab, as, 0)
+      bv += z[j] * av;
+      bb += z[j] * ab + bt[j] * av;
+      if (j > 0) {
+        bs += z[j] * as + st[j] * av;
+        bss += R(2) * st[j] * as;
+      } else {
+        bs += z[j] * as;
+      }
+      asm volatile("" ::: "memory");
+    }
+    // (z_i, bt_i, st_i, 0) * (bv, bb, bs, bss)
+    uv += z[i] * bv;
+    ub += z[i] * bb + bt[i] * bv;
+    if (i > 0) {
+      us += z[i] * bs + st[i] * bv;
+      uss += z[i] * bss + R(2) * st[i] * bs;
+    } else {
+      us += z[i] * bs;
+      uss += z[i] * bss;
+    }
+  }
+  (void)us;
+  u = uv;
+  gen = ub + R(0.5) * ((R(1) - a.rho) * diag + a.rho * uss);
+}
+
+template <int VK, int EV, typename R, int D>
+__global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R, D> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int DP = D + 1;
   const int tid = threadIdx.x;
@@ -151,20 +252,25 @@ __global__ void __launch_bounds__(256) k_paths(const __grid_constant__ Args<R, D
   const int i = item / a.chunks;
   const int chunk = item - i * a.chunks;
 
-  // shared memory carve-up
+  // shared memory carve-up (dense evaluation: no multi-index or Chebyshev
+  // tables; alpha holds the monomial coefficients, p of them)
   R* tab = reinterpret_cast<R*>(smem_raw);                         // N x tab_stride
   R* s_alpha = tab + (size_t)a.N * a.tab_stride;                   // p
   R* s_cp = s_alpha + a.p;                                          // DP x DP
   size_t off = ((size_t)a.N * a.tab_stride + a.p + DP * DP) * sizeof(R);
   off = (off + 15) & ~(size_t)15;
   uint2* s_pairs = reinterpret_cast<uint2*>(smem_raw + off);
-  off += (size_t)a.p * sizeof(uint2);
   uint8_t* s_nnz = smem_raw + off;
-  off += ((size_t)a.p + 15) & ~(size_t)15;
   R* cheb = reinterpret_cast<R*>(smem_raw + off);                  // 5 x DP x eta x tpb
   const int S = DP * a.eta * tpb;
-  off += (size_t)5 * S * sizeof(R);
-  off = (off + 15) & ~(size_t)15;
+  if constexpr (EV == EV_TABLES) {
+    off += (size_t)a.p * sizeof(uint2);
+    s_nnz = smem_raw + off;
+    off += ((size_t)a.p + 15) & ~(size_t)15;
+    cheb = reinterpret_cast<R*>(smem_raw + off);
+    off += (size_t)5 * S * sizeof(R);
+    off = (off + 15) & ~(size_t)15;
+  }
   double* red = reinterpret_cast<double*>(smem_raw + off);          // 32
 
   const R ti = (R)a.pt[i];
@@ -174,23 +280,27 @@ __global__ void __launch_bounds__(256) k_paths(const __grid_constant__ Args<R, D
   const R h = (a.T - ti) / (R)a.N;
   const R sqh = Math<R>::sqrt(h);
 
-  // per-step time factors of the local volatility
+  // per-step time factors of the local volatility (in the precision of the
+  // path: accurate sinf/expf for FP32, sin/exp for FP64)
   for (int idx = tid; idx < a.N * a.tab_stride; idx += tpb) {
     const int s = idx / a.tab_stride, j = idx - s * a.tab_stride;
-    const double ts = (double)ti + (double)s * (double)h;
+    const R ts = ti + (R)s * h;
     R v = 0;
     if constexpr (VK == VK_TANH) {
-      v = a.vol_sin ? (R)((double)a.vb * sin((double)(j + 1) + ts)) : (R)((double)a.vb * exp(-ts));
+      v = a.vol_sin ? a.vb * Math<R>::sin((R)(j + 1) + ts) : a.vb * Math<R>::exp_acc(-ts);
     } else if constexpr (VK == VK_DUPIRE) {
-      const double ew = exp(-0.05 * sqrt(ts));
-      v = (j == 0) ? (R)(0.72 * ew) : (j == 1) ? (R)(0.6 * exp(-0.1 * ts) * ew) : (R)exp((double)a.r * ts);
+      const R ew = Math<R>::exp_acc(R(-0.05) * Math<R>::sqrt(ts));
+      v = (j == 0) ? R(0.72) * ew
+                   : (j == 1) ? R(0.6) * Math<R>::exp_acc(R(-0.1) * ts) * ew : Math<R>::exp_acc(a.r * ts);
     }
     tab[idx] = v;
   }
   for (int l = tid; l < a.p; l += tpb) {
     s_alpha[l] = a.alpha[l];
-    s_pairs[l] = a.pairs[l];
-    s_nnz[l] = a.nnz[l];
+    if constexpr (EV == EV_TABLES) {
+      s_pairs[l] = a.pairs[l];
+      s_nnz[l] = a.nnz[l];
+    }
   }
   for (int q = tid; q < DP * DP; q += tpb) s_cp[q] = (&a.Cp[0][0])[q];
   __syncthreads();
@@ -274,47 +384,63 @@ __global__ void __launch_bounds__(256) k_paths(const __grid_constant__ Args<R, D
     }
     const R tau = ti + ((R)sstar + theta) * h;
 
-    // per-thread Chebyshev tables: value, drift- and diffusion-scaled
-    // derivatives at (tau, X_tau), value at (T, X_T)
-    R* tb = cheb + tid;
-#pragma unroll
-    for (int v = 0; v < DP; ++v) {
-      const R xi = (v == 0) ? (tau - a.ctr[0]) * a.sc[0] : (Xtau[v - 1] - a.ctr[v]) * a.sc[v];
-      const R xT = (v == 0) ? (a.T - a.ctr[0]) * a.sc[0] : (X[v - 1] - a.ctr[v]) * a.sc[v];
-      const R bt = (v == 0) ? a.sc[0] : drift_s[v - 1] * a.sc[v];
-      const R st = (v == 0) ? R(0) : sig_s[v - 1] * a.sc[v];
-      R t0 = 1, t1 = xi, d0 = 0, d1 = 1, e0 = 0, e1 = 0, T0 = 1, T1 = xT;
-      for (int e = 1; e <= a.eta; ++e) {
-        if (e >= 2) {
-          const R t2 = R(2) * xi * t1 - t0;
-          const R d2 = R(2) * t1 + R(2) * xi * d1 - d0;
-          const R e2 = R(4) * d1 + R(2) * xi * e1 - e0;
-          const R T2 = R(2) * xT * T1 - T0;
-          t0 = t1; t1 = t2; d0 = d1; d1 = d2; e0 = e1; e1 = e2; T0 = T1; T1 = T2;
-        }
-        const int base = (v * a.eta + e - 1) * tpb;
-        tb[base] = t1;
-        tb[base + S] = bt * d1;
-        tb[base + 2 * S] = st * d1;
-        tb[base + 3 * S] = st * st * e1;
-        tb[base + 4 * S] = T1;
-      }
-    }
     R u = 0, gsum = 0, uT = 0;
-    const R* tbr = cheb;
-    for (int l = 0; l < a.p; ++l) {
-      const R al = s_alpha[l];
-      const uint2 pr = s_pairs[l];
-      switch (s_nnz[l]) {
-        case 0: term<0, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
-        case 1: term<1, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
-        case 2: term<2, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
-        case 3: term<3, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
-        case 4: term<4, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
-        case 5: term<5, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
-        case 6: term<6, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
-        case 7: term<7, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
-        default: term<8, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+    if constexpr (EV == EV_DENSE3) {
+      R z[DP], zT[DP], bt[DP], st[DP];
+      z[0] = (tau - a.ctr[0]) * a.sc[0];
+      zT[0] = (a.T - a.ctr[0]) * a.sc[0];
+      bt[0] = a.sc[0];
+      st[0] = R(0);
+#pragma unroll
+      for (int v = 1; v < DP; ++v) {
+        z[v] = (Xtau[v - 1] - a.ctr[v]) * a.sc[v];
+        zT[v] = (X[v - 1] - a.ctr[v]) * a.sc[v];
+        bt[v] = drift_s[v - 1] * a.sc[v];
+        st[v] = sig_s[v - 1] * a.sc[v];
+      }
+      eval_dense3<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
+    } else {
+      // per-thread Chebyshev tables: value, drift- and diffusion-scaled
+      // derivatives at (tau, X_tau), value at (T, X_T)
+      R* tb = cheb + tid;
+  #pragma unroll
+      for (int v = 0; v < DP; ++v) {
+        const R xi = (v == 0) ? (tau - a.ctr[0]) * a.sc[0] : (Xtau[v - 1] - a.ctr[v]) * a.sc[v];
+        const R xT = (v == 0) ? (a.T - a.ctr[0]) * a.sc[0] : (X[v - 1] - a.ctr[v]) * a.sc[v];
+        const R bt = (v == 0) ? a.sc[0] : drift_s[v - 1] * a.sc[v];
+        const R st = (v == 0) ? R(0) : sig_s[v - 1] * a.sc[v];
+        R t0 = 1, t1 = xi, d0 = 0, d1 = 1, e0 = 0, e1 = 0, T0 = 1, T1 = xT;
+        for (int e = 1; e <= a.eta; ++e) {
+          if (e >= 2) {
+            const R t2 = R(2) * xi * t1 - t0;
+            const R d2 = R(2) * t1 + R(2) * xi * d1 - d0;
+            const R e2 = R(4) * d1 + R(2) * xi * e1 - e0;
+            const R T2 = R(2) * xT * T1 - T0;
+            t0 = t1; t1 = t2; d0 = d1; d1 = d2; e0 = e1; e1 = e2; T0 = T1; T1 = T2;
+          }
+          const int base = (v * a.eta + e - 1) * tpb;
+          tb[base] = t1;
+          tb[base + S] = bt * d1;
+          tb[base + 2 * S] = st * d1;
+          tb[base + 3 * S] = st * st * e1;
+          tb[base + 4 * S] = T1;
+        }
+      }
+      const R* tbr = cheb;
+      for (int l = 0; l < a.p; ++l) {
+        const R al = s_alpha[l];
+        const uint2 pr = s_pairs[l];
+        switch (s_nnz[l]) {
+          case 0: term<0, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+          case 1: term<1, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+          case 2: term<2, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+          case 3: term<3, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+          case 4: term<4, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+          case 5: term<5, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+          case 6: term<6, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+          case 7: term<7, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+          default: term<8, R>(tbr, S, a.eta, tpb, tid, pr, s_cp, DP, al, u, gsum, uT); break;
+        }
       }
     }
     const R obs = basket_value<R, D>(a, Xtau, a.obstacle == 0);
@@ -337,17 +463,30 @@ __global__ void __launch_bounds__(256) k_paths(const __grid_constant__ Args<R, D
   }
 }
 
-inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize) {
+// dynamic shared memory of the path kernel; dense: p is the number of
+// monomial coefficients and there are no per-thread tables
+inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bool dense) {
   const int dp = d + 1;
   const int tab_stride = d < 3 ? 3 : d;
   size_t off = ((size_t)N * tab_stride + p + dp * dp) * rsize;
   off = (off + 15) & ~(size_t)15;
-  off += (size_t)p * sizeof(uint2);
-  off += ((size_t)p + 15) & ~(size_t)15;
-  off += (size_t)5 * dp * eta * tpb * rsize;
-  off = (off + 15) & ~(size_t)15;
+  if (!dense) {
+    off += (size_t)p * sizeof(uint2);
+    off += ((size_t)p + 15) & ~(size_t)15;
+    off += (size_t)5 * dp * eta * tpb * rsize;
+    off = (off + 15) & ~(size_t)15;
+  }
   off += 32 * sizeof(double);
   return off;
+}
+
+template <int VK, int EV, typename R, int D>
+cudaError_t launch_one(const Args<R, D>& a, unsigned grid, int tpb, size_t smem, cudaStream_t st) {
+  cudaError_t err =
+      cudaFuncSetAttribute(k_paths<VK, EV, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_paths<VK, EV, R, D><<<grid, tpb, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 template <typename R, int D>
@@ -361,6 +500,7 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.K = (R)m.K;
   a.s_dupire = (R)m.s_dupire;
   a.vb = (R)m.b;
+  a.rho = (R)(m.d > 1 ? m.C[1] : 0.0);
   for (int j = 0; j < D; ++j) {
     a.rd[j] = (R)(m.r - m.div[j]);
     a.w[j] = (R)m.w[j];
@@ -399,27 +539,25 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.pairs = P.pairs;
   a.nnz = P.nnz;
   a.partial = P.partial;
-  const size_t smem = smem_bytes(D, P.p, a.eta, N, tpb, sizeof(R));
+  const bool dense = P.dense;
+  if (dense) {
+    a.p = P.pm;
+    if constexpr (sizeof(R) == 4)
+      a.alpha = reinterpret_cast<const R*>(P.beta32);
+    else
+      a.alpha = reinterpret_cast<const R*>(P.beta);
+  }
+  const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense);
   const int vk = (m.vol_kind == 0) ? VK_CONST : (m.vol_kind == 3) ? VK_DUPIRE : VK_TANH;
   const unsigned grid = (unsigned)P.n * (unsigned)P.chunks;
-  cudaError_t err = cudaSuccess;
-  if (vk == VK_CONST) {
-    err = cudaFuncSetAttribute(k_paths<VK_CONST, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-    if (err != cudaSuccess) return err;
-    k_paths<VK_CONST, R, D><<<grid, tpb, smem, st>>>(a);
-  } else if (vk == VK_TANH) {
-    err = cudaFuncSetAttribute(k_paths<VK_TANH, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-    if (err != cudaSuccess) return err;
-    k_paths<VK_TANH, R, D><<<grid, tpb, smem, st>>>(a);
-  } else {
-    err = cudaFuncSetAttribute(k_paths<VK_DUPIRE, R, D>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    k_paths<VK_DUPIRE, R, D><<<grid, tpb, smem, st>>>(a);
+  if (dense) {
+    if (vk == VK_CONST) return launch_one<VK_CONST, EV_DENSE3>(a, grid, tpb, smem, st);
+    if (vk == VK_TANH) return launch_one<VK_TANH, EV_DENSE3>(a, grid, tpb, smem, st);
+    return launch_one<VK_DUPIRE, EV_DENSE3>(a, grid, tpb, smem, st);
   }
-  return cudaGetLastError();
+  if (vk == VK_CONST) return launch_one<VK_CONST, EV_TABLES>(a, grid, tpb, smem, st);
+  if (vk == VK_TANH) return launch_one<VK_TANH, EV_TABLES>(a, grid, tpb, smem, st);
+  return launch_one<VK_DUPIRE, EV_TABLES>(a, grid, tpb, smem, st);
 }
 
 }  // namespace paths

@@ -62,3 +62,67 @@ bool pack_multi_indices(const std::vector<std::vector<int>>& nus, std::vector<ui
   }
   return true;
 }
+
+// Chebyshev -> monomial map of a basis of total degree <= 3.  Monomials in
+// the order constant, z_a, z_a z_b (a <= b), z_a z_b z_c (a <= b <= c), each
+// group lexicographic.  T_1 = z, T_2 = 2 z^2 - 1, T_3 = 4 z^3 - 3 z.
+int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, std::vector<int>& row,
+                       std::vector<int>& lidx, std::vector<double>& coef) {
+  // index of each sorted multiset of variates
+  std::vector<std::vector<int>> monos;
+  monos.push_back({});
+  for (int a = 0; a < dp; ++a) monos.push_back({a});
+  for (int a = 0; a < dp; ++a)
+    for (int b = a; b < dp; ++b) monos.push_back({a, b});
+  for (int a = 0; a < dp; ++a)
+    for (int b = a; b < dp; ++b)
+      for (int c = b; c < dp; ++c) monos.push_back({a, b, c});
+  const int pm = (int)monos.size();
+  auto index_of = [&](const std::vector<int>& ms) {
+    for (int m = 0; m < pm; ++m)
+      if (monos[m] == ms) return m;
+    return -1;
+  };
+  std::vector<std::vector<std::pair<int, double>>> rows(pm);
+  // expansion of T_e as (power, coefficient)
+  const std::vector<std::pair<int, double>> cheb[4] = {
+      {{0, 1.0}}, {{1, 1.0}}, {{0, -1.0}, {2, 2.0}}, {{1, -3.0}, {3, 4.0}}};
+  for (size_t l = 0; l < nus.size(); ++l) {
+    int deg = 0;
+    for (int e : nus[l]) deg += e;
+    if (deg > 3) return -1;
+    // cartesian product over the variates
+    std::vector<std::pair<std::vector<int>, double>> terms = {{std::vector<int>(dp, 0), 1.0}};
+    for (int v = 0; v < dp; ++v) {
+      const int e = nus[l][v];
+      if (e == 0) continue;
+      std::vector<std::pair<std::vector<int>, double>> next;
+      for (const auto& t : terms)
+        for (const auto& pc : cheb[e]) {
+          auto mu = t.first;
+          mu[v] = pc.first;
+          next.push_back({mu, t.second * pc.second});
+        }
+      terms.swap(next);
+    }
+    for (const auto& t : terms) {
+      std::vector<int> ms;
+      for (int v = 0; v < dp; ++v)
+        for (int q = 0; q < t.first[v]; ++q) ms.push_back(v);
+      const int m = index_of(ms);
+      if (m < 0) return -1;
+      rows[m].push_back({(int)l, t.second});
+    }
+  }
+  row.assign(pm + 1, 0);
+  lidx.clear();
+  coef.clear();
+  for (int m = 0; m < pm; ++m) {
+    for (const auto& e : rows[m]) {
+      lidx.push_back(e.first);
+      coef.push_back(e.second);
+    }
+    row[m + 1] = (int)lidx.size();
+  }
+  return pm;
+}

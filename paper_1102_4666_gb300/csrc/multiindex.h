@@ -13,3 +13,9 @@ std::vector<std::vector<int>> build_multi_indices(int dp, int eta, double q);
 // or degree exceeds 15 or more than 8 variates are active
 bool pack_multi_indices(const std::vector<std::vector<int>>& nus, std::vector<uint32_t>& pairs_xy,
                         std::vector<uint8_t>& nnz, int& max_deg);
+
+// Chebyshev -> monomial map (CSR by monomial) of a basis of total degree
+// <= 3; returns the number of monomials C(dp + 3, 3), or -1 when a basis
+// function has a larger degree
+int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, std::vector<int>& row,
+                       std::vector<int>& lidx, std::vector<double>& coef);

@@ -146,17 +146,19 @@ void Problem::ensure_events(int count) {
 
 // launch shape of the path kernel: threads per CTA and paths per thread,
 // limited by the shared memory of the per-thread Chebyshev tables
-int Problem::choose_launch(int d, int p, int eta, int N, int M, bool mx, int& tpb, int& ppt) {
+int Problem::choose_launch(int d, int p, int eta, int N, int M, bool mx, bool dense, int& tpb,
+                           int& ppt) {
   tpb = mx ? 128 : 64;
-  while (tpb > 32 && paths_smem_bytes(d, p, eta, N, tpb, mx) > 220 * 1024) tpb >>= 1;
-  if (paths_smem_bytes(d, p, eta, N, tpb, mx) > 220 * 1024) return BSDE_ERR_INVALID_ARG;
+  while (tpb > 32 && paths_smem_bytes(d, p, eta, N, tpb, mx, dense) > 220 * 1024) tpb >>= 1;
+  if (paths_smem_bytes(d, p, eta, N, tpb, mx, dense) > 220 * 1024) return BSDE_ERR_INVALID_ARG;
   // about 512 paths per CTA, fewer for small M
   ppt = 4;
   while (ppt > 1 && (long long)tpb * ppt > 2LL * M) ppt >>= 1;
   return BSDE_OK;
 }
 
-size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int tpb, int ppt) {
+size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int tpb, int ppt, int pm,
+                               int conv_nnz) {
   (void)N;
   const int n_pad = (n + 31) / 32 * 32;
   const int p_pad = (p + 127) / 128 * 128;
@@ -186,6 +188,13 @@ size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int t
   add((size_t)p);
   add(64);
   add((OUT_SIZE + 1 + 2 * BSDE_DMAX) * 8);
+  if (pm > 0) {
+    add((size_t)pm * 8);
+    add((size_t)pm * 4);
+    add((size_t)(pm + 1) * 4);
+    add((size_t)conv_nnz * 4);
+    add((size_t)conv_nnz * 8);
+  }
   return b;
 }
 
@@ -218,6 +227,8 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     }
     eta_used = mdeg;
     coeffs_valid = false;
+    pm = build_cheb_to_mono(nus, d + 1, conv_row, conv_l, conv_c);
+    if (pm < 0) pm = 0;
   }
   const int p = (int)nus.size();
   const int n = grid.n;
@@ -237,13 +248,45 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   s.M = prm.M;
   s.N = prm.N_steps;
   s.mixed = mixed;
-  if (choose_launch(d, p, s.eta, s.N, s.M, mixed, s.tpb, s.ppt) != BSDE_OK) {
+  if (prm.eval_mode == 2 && pm == 0) {
+    err = "solve: eval_mode 2 (dense) needs a basis of total degree <= 3";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  // the dense evaluation needs a constant correlation (all off-diagonal
+  // entries equal)
+  bool const_corr = true;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      if (i != j && model.C[i * d + j] != model.C[1]) const_corr = false;
+  if (prm.eval_mode == 2 && !const_corr) {
+    err = "solve: eval_mode 2 (dense) needs a constant correlation";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  s.dense = pm > 0 && const_corr && prm.eval_mode != 1;
+  s.pm = s.dense ? pm : 0;
+  if (choose_launch(d, s.dense ? pm : p, s.eta, s.N, s.M, mixed, s.dense, s.tpb, s.ppt) != BSDE_OK) {
     err = "solve: basis and step count too large for the shared-memory tables";
     return BSDE_ERR_INVALID_ARG;
   }
+  if (prm.paths_tpb) {
+    if (prm.paths_tpb < 32 || prm.paths_tpb > 256 || prm.paths_tpb % 32 ||
+        paths_smem_bytes(d, s.dense ? pm : p, s.eta, s.N, prm.paths_tpb, mixed, s.dense) > 220 * 1024) {
+      err = "solve: paths_tpb must be a multiple of 32 in 32..256 within the shared memory";
+      return BSDE_ERR_INVALID_ARG;
+    }
+    s.tpb = prm.paths_tpb;
+  }
+  if (prm.paths_ppt) {
+    if (prm.paths_ppt < 1 || prm.paths_ppt > 16) {
+      err = "solve: paths_ppt must be in 1..16";
+      return BSDE_ERR_INVALID_ARG;
+    }
+    s.ppt = prm.paths_ppt;
+  }
   s.chunks = (s.M + s.tpb * s.ppt - 1) / (s.tpb * s.ppt);
   if (!block || !(s == alloc_shape)) {
-    const size_t need = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt);
+    const size_t need = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt, s.pm,
+                                       s.dense ? (int)conv_l.size() : 0);
     if (budget && need > budget) {
       std::ostringstream os;
       os << "solve: needs " << need << " bytes of device memory, budget " << budget;
@@ -305,6 +348,15 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     P.key = (uint32_t*)take(64);
     P.status = (int*)(P.key + 4);
     P.out = (double*)take((OUT_SIZE + 1 + 2 * BSDE_DMAX) * 8);
+    if (s.dense) {
+      P.dense = true;
+      P.pm = s.pm;
+      P.beta = (double*)take((size_t)s.pm * 8);
+      P.beta32 = (float*)take((size_t)s.pm * 4);
+      P.conv_row = (int*)take((size_t)(s.pm + 1) * 4);
+      P.conv_l = (int*)take(conv_l.size() * 4);
+      P.conv_c = (double*)take(conv_c.size() * 8);
+    }
     dev = P;
     coeffs_valid = false;
   }
@@ -313,6 +365,13 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   // tables, read-out point, key
   cudaError_t e = cudaMemcpyAsync(dev.pairs, pairs.data(), (size_t)p * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dev.nnz, nnz.data(), (size_t)p, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && dev.dense) {
+    e = cudaMemcpyAsync(dev.conv_row, conv_row.data(), conv_row.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dev.conv_l, conv_l.data(), conv_l.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dev.conv_c, conv_c.data(), conv_c.size() * 8, cudaMemcpyHostToDevice, st);
+  }
   double logS0[BSDE_DMAX];
   for (int j = 0; j < d; ++j) logS0[j] = std::log(model.S0[j]);
   if (e == cudaSuccess)
@@ -344,6 +403,7 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
   const uint32_t kp = grid.resample ? (uint32_t)k : 0u;
   launch_points(model, grid, dev, kp, st);
   launch_basis(model, grid, dev, mixed, st);
+  if (dev.dense) launch_cheb2mono(dev, st);
   if (rec) record(ev[0], st);
   cudaError_t e = launch_paths(model, grid, dev, shape.M, shape.N, (uint32_t)k, mixed, shape.tpb,
                                shape.ppt, st);
@@ -523,7 +583,7 @@ int Problem::finish_report(const bsde_solve_params& prm, cudaStream_t st, bsde_r
     const int panels = (shape.p + 31) / 32;
     const int chol = 1 + 3 * panels - 2;
     r.kernel_launches =
-        prm.K_it * (2 + 1 + 1 + (mixed ? 2 : 1) + 1 + chol + 1 + refine * 3 + 1 + 3);
+        prm.K_it * (2 + (dev.dense ? 1 : 0) + 1 + 1 + (mixed ? 2 : 1) + 1 + chol + 1 + refine * 3 + 1 + 3);
     // points, basis, paths, reduce, Gram (+ reduce), rhs, Cholesky, solve,
     // refinement (2 GEMVs + solve each), update, read-out (3)
     if (prm.timing && (int)events.size() >= 6 * prm.K_it) {

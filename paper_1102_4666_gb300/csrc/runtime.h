@@ -21,11 +21,11 @@ struct Allocator {
 
 struct Shape {
   int d = 0, n = 0, n_pad = 0, p = 0, p_pad = 0, eta = 0, M = 0, N = 0;
-  int chunks = 0, tpb = 0, ppt = 0, splits = 0;
-  bool mixed = false;
+  int chunks = 0, tpb = 0, ppt = 0, splits = 0, pm = 0;
+  bool mixed = false, dense = false;
   bool operator==(const Shape& o) const {
     return d == o.d && n == o.n && p == o.p && eta == o.eta && M == o.M && N == o.N &&
-           tpb == o.tpb && ppt == o.ppt && mixed == o.mixed;
+           tpb == o.tpb && ppt == o.ppt && mixed == o.mixed && dense == o.dense && pm == o.pm;
   }
 };
 
@@ -41,6 +41,10 @@ class Problem {
   std::vector<uint8_t> nnz;
   std::vector<std::vector<int>> nus;
   int eta_used = 0;  // largest single-variate degree present
+  // Chebyshev -> monomial map when the total degree is <= 3 (pm > 0)
+  int pm = 0;
+  std::vector<int> conv_row, conv_l;
+  std::vector<double> conv_c;
   std::string err;
 
   ~Problem();
@@ -63,7 +67,8 @@ class Problem {
   void release(Allocator& al, cudaStream_t st);
   void destroy_graph();  // after a model or grid change
   size_t bytes() const { return block_bytes; }
-  static size_t estimate_bytes(int d, int n, int p, int M, int N, bool mixed, int tpb, int ppt);
+  static size_t estimate_bytes(int d, int n, int p, int M, int N, bool mixed, int tpb, int ppt,
+                               int pm = 0, int conv_nnz = 0);
 
  private:
   void* block = nullptr;
@@ -73,7 +78,8 @@ class Problem {
   cudaGraphExec_t gexec = nullptr;
   std::string graph_key;
   std::vector<cudaEvent_t> events;  // 6 per iteration when timing
-  int choose_launch(int d, int p, int eta, int N, int M, bool mixed, int& tpb, int& ppt);
+  int choose_launch(int d, int p, int eta, int N, int M, bool mixed, bool dense, int& tpb,
+                    int& ppt);
   void ensure_events(int count);
 };
 

@@ -133,13 +133,18 @@ def _scale(cfg, nu, alpha, t, x):
     return max(1.0, cfg["K"] * 0.5, np.max(np.abs(u)) * (1.0 + cfg["lambda"] * cfg["T"]))
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_teacher_forced_iteration_fp64(G, name):
+# (case, eval_mode): 0 automatic (dense monomial form for total degree <= 3
+# and constant correlation), 1 per-thread Chebyshev tables
+EVAL_CASES = [(n, 0) for n in CASES] + [(n, 1) for n in CASES if CASES[n][1]["eta"] <= 3]
+
+
+@pytest.mark.parametrize("name,ev", EVAL_CASES)
+def test_teacher_forced_iteration_fp64(G, name, ev):
     cfg = _case(name)
     nu = O.multi_index_set(cfg["d"] + 1, cfg["eta"])
     a0 = _alpha(cfg, nu)
     s = solver(G, cfg, "fp64")
-    t, x, c, a1 = s.iterate(2, a0)
+    t, x, c, a1 = s.iterate(2, a0, eval_mode=ev)
     s.close()
     it = O.iteration(cfg, nu, a0, 2, nthreads=NTH)
     sc = _scale(cfg, nu, a0, t, x)
@@ -147,13 +152,13 @@ def test_teacher_forced_iteration_fp64(G, name):
     assert rel(a1 - a0, it["alpha"] - a0) < 1e-8
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_teacher_forced_iteration_mixed(G, name):
+@pytest.mark.parametrize("name,ev", EVAL_CASES)
+def test_teacher_forced_iteration_mixed(G, name, ev):
     cfg = _case(name)
     nu = O.multi_index_set(cfg["d"] + 1, cfg["eta"])
     a0 = _alpha(cfg, nu)
     s = solver(G, cfg, "mixed")
-    t, x, c, a1 = s.iterate(2, a0)
+    t, x, c, a1 = s.iterate(2, a0, eval_mode=ev)
     s.close()
     it = O.iteration(cfg, nu, a0, 2, nthreads=NTH)
     sc = _scale(cfg, nu, a0, t, x)
@@ -181,7 +186,8 @@ def test_refit_solves_the_normal_equations(G, prec):
     assert rel(a1 - a0, delta) < 1e-9
 
 
-def test_full_size_c4_sampled_points(G):
+@pytest.mark.parametrize("ev", [0, 1])
+def test_full_size_c4_sampled_points(G, ev):
     """c4 at its full size (n=4000, M=4000, N=100, p=364), one mixed
     iteration in the bench's launch configuration; the oracle recomputes
     c_i at a sample of points."""
@@ -189,7 +195,7 @@ def test_full_size_c4_sampled_points(G):
     nu = O.multi_index_set(11, 3)
     a0 = _alpha(cfg, nu, scale=1.0)
     s = solver(G, cfg, "mixed")
-    t, x, c, a1 = s.iterate(5, a0)
+    t, x, c, a1 = s.iterate(5, a0, eval_mode=ev)
     s.close()
     idx = np.arange(0, 4000, 500)
     co = O.correction(cfg, nu, a0, 5, idx, t[idx], x[:, idx], nthreads=NTH)
