@@ -236,6 +236,50 @@ BSDE_API int bsde_eval_price_delta(bsde_ctx* ctx, int q, const double* t, const 
                           double* delta);
 
 /* ------------------------------------------------------------------------
+ * No-allocation entry point.  The paper has no counterpart: it serves
+ * callers of this library that cannot allocate device memory themselves or
+ * through the library -- code that runs inside a fixed device-memory arena,
+ * a plugin whose host process forbids cudaMalloc/cudaFree, or a steady-state
+ * service loop that must never enter the allocator.
+ *
+ * bsde_corrections_noalloc computes the Monte Carlo corrections c^k_i of
+ * eq. chat (Algorithm 2) at n given points with the path kernel, like
+ * c_out of bsde_iterate with eval_mode 1, and calls no allocating routine
+ * (no cudaMalloc, cudaFree, PyTorch or other allocator).  Inputs and outputs
+ * are the caller's device buffers: t_dev (n), x_dev (d x n, row j holding
+ * x_j of every point), alpha_dev (p FP64 coefficients in the order of
+ * bsde_basis_indices for (d, eta, q)) and c_dev (n outputs).  The model and
+ * the box (lo, hi: d+1 host values each) are as in bsde_set_model and
+ * bsde_set_grid; M, N_steps, seed and the iteration index k as in a solve;
+ * precision is BSDE_PREC_FP64 or BSDE_PREC_MIXED.  Works on the current
+ * CUDA device and on `stream` (NULL: the legacy default stream); it returns
+ * after the stream has finished the work.
+ *
+ * The kernel's scratch (per-chunk partial sums, the packed basis table, the
+ * FP32 coefficient copy, the Philox key) is one static 4 MiB device array
+ * that every GPU loading the library holds until the process exits.  Limits:
+ * p <= 4096 basis functions and n * ceil(M / C) <= 503808, where C is the
+ * number of paths per chunk that the path kernel uses (512 in MIXED and 256
+ * in FP64 precision when M >= 256 and the basis tables fit; fewer for small
+ * M or large bases); larger problems are rejected with BSDE_ERR_NOMEM
+ * before any device work.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call uses the same array
+ * and the array keeps the last call's contents; each call rewrites every
+ * scratch word it reads, so nothing needs clearing, but calls that overlap
+ * on the GPU (other streams, other host threads) race on the array and must
+ * be serialised by the caller.  errbuf (optional, errbuf_len bytes) receives
+ * a message on failure.  Errors: BSDE_ERR_INVALID_ARG, BSDE_ERR_NOMEM (too
+ * large for the scratch), BSDE_ERR_CUDA. */
+BSDE_API int bsde_corrections_noalloc(const bsde_sigma* sigma, double r, const bsde_payoff* payoff,
+                                      const bsde_penalty* penalty, const double* lo,
+                                      const double* hi, int n, const double* t_dev,
+                                      const double* x_dev, int eta, double q,
+                                      const double* alpha_dev, int M, int N_steps, uint64_t seed,
+                                      int k, int precision, double* c_dev, void* stream,
+                                      char* errbuf, size_t errbuf_len);
+
+/* ------------------------------------------------------------------------
  * Serving: a continuous-batching server of pricing requests.  Requests of
  * uneven d, n, M, N and degree are admitted while device memory (the
  * server's budget) and slots allow; each keeps its coefficients and points

@@ -130,6 +130,11 @@ _SIGNATURES = {
     "bsde_set_coeffs": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bsde_solve_params), _dptr,
                                        ctypes.c_int]),
     "bsde_eval_price_delta": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dptr, _dptr, _dptr, _dptr]),
+    "bsde_corrections_noalloc": (ctypes.c_int, [
+        ctypes.POINTER(bsde_sigma), ctypes.c_double, ctypes.POINTER(bsde_payoff), ctypes.POINTER(bsde_penalty),
+        _dptr, _dptr, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]),
     "bsde_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(bsde_server_opts)]),
     "bsde_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bsde_request),
                                           ctypes.POINTER(ctypes.c_uint64)]),
