@@ -46,7 +46,7 @@ struct Philox {
 };
 
 // ---------------------------------------------------------------------------
-// Precision traits: the FP32 path uses the fast hardware approximations
+// Precision traits (Box-Muller returns scale * (z0, z1)): the FP32 path uses the fast hardware approximations
 // (MUFU) where their error is far below the Monte Carlo noise; the FP64 path
 // uses CUDA's double-precision math library.
 // ---------------------------------------------------------------------------
@@ -57,12 +57,12 @@ template <>
 struct Math<float> {
   // Box-Muller pair from two 32-bit words: u = (w + 1/2) 2^-32 in (0,1]
   __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, float& z0,
-                                                    float& z1) {
+                                                    float& z1, float scale) {
     const float u0 = fmaf(__uint2float_rn(w0), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float u1 = fmaf(__uint2float_rn(w1), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     // sqrt(r2) as r2 * rsqrt(r2) (r2 >= 1e-30 keeps rsqrt finite)
     const float r2 = fmaxf(-2.0f * __logf(u0), 1e-30f);
-    const float rad = r2 * rsqrtf(r2);
+    const float rad = r2 * rsqrtf(r2) * scale;
     float s, c;
     // angle 2 pi u1 - pi keeps the argument in (-pi, pi]; cos/sin flip sign
     __sincosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f), &s, &c);
@@ -84,10 +84,10 @@ struct Math<float> {
 template <>
 struct Math<double> {
   __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, double& z0,
-                                                    double& z1) {
+                                                    double& z1, double scale) {
     const double u0 = ((double)w0 + 0.5) * 2.3283064365386962890625e-10;
     const double u1 = ((double)w1 + 0.5) * 2.3283064365386962890625e-10;
-    const double rad = ::sqrt(-2.0 * ::log(u0));
+    const double rad = ::sqrt(-2.0 * ::log(u0)) * scale;
     double s, c;
     sincospi(2.0 * u1, &s, &c);
     z0 = rad * c;

@@ -43,12 +43,14 @@ struct Args {
   R rd[D];          // r - delta_j
   R w[D], va[D], kappa[D];
   R L[D][D];        // lower Cholesky factor of the correlation
+  R Ld[D], Lc[D];   // constant correlation: diagonal of L and its constant column below it
   R Cp[D + 1][D + 1];  // correlation padded with a zero time row/column
   R ctr[D + 1], sc[D + 1];  // xi_v = (y_v - ctr_v) sc_v
   int N, M, n, p, eta, chunks, tpb, ppt, tab_stride;
   int payoff, obstacle, absflag, vol_sin;
   R vb;
   R rho;  // constant correlation (dense evaluation)
+  R kc[D];  // -2 log2(e) kappa_j: e^{2 (x - kappa)} = 2^{x 2 log2(e) + kc}
   uint32_t k;
   const uint32_t* key;
   const double* pt;
@@ -72,15 +74,32 @@ __device__ __forceinline__ double uniform_frac<double>(uint32_t w) {
   return ((double)w + 0.5) * 2.3283064365386962890625e-10;
 }
 
-// local volatility of asset j at the step whose table row is tabs
+// r = 1 / (e^{2 (x - kappa_j)} + 1), so that tanh(x - kappa_j) = 1 - 2 r
+template <typename R, int D>
+__device__ __forceinline__ R tanh_r(const Args<R, D>& a, int j, R xj) {
+  if constexpr (sizeof(R) == 4) {
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(xj, 2.8853900817779268f, a.kc[j])));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.0f));
+    return r;
+  } else {
+    return 1.0 / (::exp(2.0 * (xj - a.kappa[j])) + 1.0);
+  }
+}
+
+// local volatility of asset j at the step whose table row is tabs.  The
+// tanh families keep (A, B) per step and asset: sigma = A + B r for
+// a + phi tanh (A = a + phi, B = -2 phi) and sigma = A + B |1 - 2 r| for
+// a + phi |tanh| (A = a, B = phi), with phi the time factor.
 template <int VK, typename R, int D>
 __device__ __forceinline__ R sigma_j(const Args<R, D>& a, const R* tabs, int j, R xj) {
   if constexpr (VK == VK_CONST) {
     return a.va[j];
   } else if constexpr (VK == VK_TANH) {
-    R th = Math<R>::tanh(xj - a.kappa[j]);
-    if (a.absflag) th = Math<R>::fabs(th);
-    return a.va[j] + tabs[j] * th;
+    const R r = tanh_r(a, j, xj);
+    const R A = tabs[2 * j], B = tabs[2 * j + 1];
+    if (a.absflag) return A + B * Math<R>::fabs(R(1) - R(2) * r);
+    return A + B * r;
   } else {
     const R dev = Math<R>::exp(xj) * tabs[2] - a.s_dupire;
     return tabs[0] - tabs[1] * Math<R>::exp(R(-0.001) * dev * dev);
@@ -242,7 +261,7 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
   gen = ub + R(0.5) * ((R(1) - a.rho) * diag + a.rho * uss);
 }
 
-template <int VK, int EV, typename R, int D>
+template <int VK, int EV, bool CC, typename R, int D>
 __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R, D> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int DP = D + 1;
@@ -280,18 +299,23 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
   const R h = (a.T - ti) / (R)a.N;
   const R sqh = Math<R>::sqrt(h);
 
-  // per-step time factors of the local volatility (in the precision of the
+  // per-step coefficients of the local volatility (in the precision of the
   // path: accurate sinf/expf for FP32, sin/exp for FP64)
   for (int idx = tid; idx < a.N * a.tab_stride; idx += tpb) {
-    const int s = idx / a.tab_stride, j = idx - s * a.tab_stride;
+    const int s = idx / a.tab_stride, c = idx - s * a.tab_stride;
     const R ts = ti + (R)s * h;
     R v = 0;
     if constexpr (VK == VK_TANH) {
-      v = a.vol_sin ? a.vb * Math<R>::sin((R)(j + 1) + ts) : a.vb * Math<R>::exp_acc(-ts);
+      const int j = c >> 1;
+      const R phi = a.vol_sin ? a.vb * Math<R>::sin((R)(j + 1) + ts) : a.vb * Math<R>::exp_acc(-ts);
+      if (a.absflag)
+        v = (c & 1) ? phi : a.va[j < D ? j : 0];
+      else
+        v = (c & 1) ? R(-2) * phi : a.va[j < D ? j : 0] + phi;
     } else if constexpr (VK == VK_DUPIRE) {
       const R ew = Math<R>::exp_acc(R(-0.05) * Math<R>::sqrt(ts));
-      v = (j == 0) ? R(0.72) * ew
-                   : (j == 1) ? R(0.6) * Math<R>::exp_acc(R(-0.1) * ts) * ew : Math<R>::exp_acc(a.r * ts);
+      v = (c == 0) ? R(0.72) * ew
+                   : (c == 1) ? R(0.6) * Math<R>::exp_acc(R(-0.1) * ts) * ew : Math<R>::exp_acc(a.r * ts);
     }
     tab[idx] = v;
   }
@@ -322,21 +346,23 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const int sstar = (int)(wN >> 32);
     const R theta = uniform_frac<R>((uint32_t)wN);
 
-    R X[D], Xs[D], dXs[D];
+    // state, and at the step s* that contains tau: X before and after it
+    R X[D], Xs[D], Xn[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       X[j] = x0[j];
       Xs[j] = x0[j];
-      dXs[j] = 0;
+      Xn[j] = x0[j];
     }
+    const R nhh = R(-0.5) * h;
     for (int s0 = 0; s0 < a.N; s0 += G) {
-      R z[G * D];
+      R z[G * D];  // normals of G steps, scaled by sqrt(h)
       const uint32_t blk0 = (uint32_t)(s0 / G) * (uint32_t)NB;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         const uint4 o = ph(blk0 + b, (uint32_t)m, (uint32_t)i, tagZ);
-        Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1]);
-        Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3]);
+        Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1], sqh);
+        Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3], sqh);
       }
 #pragma unroll
       for (int gs = 0; gs < G; ++gs) {
@@ -344,19 +370,27 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
         if (s < a.N) {
           const R* tabs = tab + s * a.tab_stride;
           const bool hit = (s == sstar);
+          R pre = 0;  // running sum of the constant-correlation factor
 #pragma unroll
           for (int j = 0; j < D; ++j) {
-            R y = 0;
+            // correlated increment y = sqrt(h) (L Z)_j
+            R y;
+            if constexpr (CC) {
+              y = a.Ld[j] * z[gs * D + j] + pre;
+              pre += a.Lc[j] * z[gs * D + j];
+            } else {
+              y = 0;
 #pragma unroll
-            for (int q = 0; q <= j; ++q) y += a.L[j][q] * z[gs * D + q];
+              for (int q = 0; q <= j; ++q) y += a.L[j][q] * z[gs * D + q];
+            }
             const R sig = sigma_j<VK>(a, tabs, j, X[j]);
-            const R drift = a.rd[j] - R(0.5) * sig * sig;
-            const R dx = drift * h + sig * sqh * y;
+            // X + (r - delta_j - sigma^2/2) h + sigma y = X + h rd_j + sigma (y - h sigma / 2)
+            const R xn = sig * (nhh * sig + y) + (h * a.rd[j] + X[j]);
             if (hit) {
               Xs[j] = X[j];
-              dXs[j] = dx;
+              Xn[j] = xn;
             }
-            X[j] += dx;
+            X[j] = xn;
           }
         }
       }
@@ -367,8 +401,8 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
 #pragma unroll
     for (int b = 0; b < NBB; ++b) {
       const uint4 o = ph((uint32_t)b, (uint32_t)m, (uint32_t)i, tagB);
-      Math<R>::box_muller(o.x, o.y, zb[4 * b + 0], zb[4 * b + 1]);
-      Math<R>::box_muller(o.z, o.w, zb[4 * b + 2], zb[4 * b + 3]);
+      Math<R>::box_muller(o.x, o.y, zb[4 * b + 0], zb[4 * b + 1], R(1));
+      Math<R>::box_muller(o.z, o.w, zb[4 * b + 2], zb[4 * b + 3], R(1));
     }
     const R* tab_s = tab + sstar * a.tab_stride;
     const R bb = Math<R>::sqrt(theta * (R(1) - theta) * h);
@@ -380,7 +414,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
       for (int q = 0; q <= j; ++q) y += a.L[j][q] * zb[q];
       sig_s[j] = sigma_j<VK>(a, tab_s, j, Xs[j]);
       drift_s[j] = a.rd[j] - R(0.5) * sig_s[j] * sig_s[j];
-      Xtau[j] = Xs[j] + theta * dXs[j] + sig_s[j] * bb * y;
+      Xtau[j] = Xs[j] + theta * (Xn[j] - Xs[j]) + sig_s[j] * bb * y;
     }
     const R tau = ti + ((R)sstar + theta) * h;
 
@@ -465,9 +499,9 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
 
 // dynamic shared memory of the path kernel; dense: p is the number of
 // monomial coefficients and there are no per-thread tables
-inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bool dense) {
+inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bool dense,
+                         int tab_stride) {
   const int dp = d + 1;
-  const int tab_stride = d < 3 ? 3 : d;
   size_t off = ((size_t)N * tab_stride + p + dp * dp) * rsize;
   off = (off + 15) & ~(size_t)15;
   if (!dense) {
@@ -480,12 +514,12 @@ inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bo
   return off;
 }
 
-template <int VK, int EV, typename R, int D>
+template <int VK, int EV, bool CC, typename R, int D>
 cudaError_t launch_one(const Args<R, D>& a, unsigned grid, int tpb, size_t smem, cudaStream_t st) {
-  cudaError_t err =
-      cudaFuncSetAttribute(k_paths<VK, EV, R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = cudaFuncSetAttribute(k_paths<VK, EV, CC, R, D>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  k_paths<VK, EV, R, D><<<grid, tpb, smem, st>>>(a);
+  k_paths<VK, EV, CC, R, D><<<grid, tpb, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -501,7 +535,14 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.s_dupire = (R)m.s_dupire;
   a.vb = (R)m.b;
   a.rho = (R)(m.d > 1 ? m.C[1] : 0.0);
+  bool cc = true;
+  for (int j = 0; j < D; ++j)
+    for (int q = 0; q < D; ++q)
+      if (j != q && m.C[j * D + q] != m.C[D > 1 ? 1 : 0]) cc = false;
   for (int j = 0; j < D; ++j) {
+    a.Ld[j] = (R)m.L[j * D + j];
+    a.Lc[j] = (R)(j + 1 < D ? m.L[(j + 1) * D + j] : 0.0);
+    a.kc[j] = (R)(-2.8853900817779268 * m.kappa[j]);
     a.rd[j] = (R)(m.r - m.div[j]);
     a.w[j] = (R)m.w[j];
     a.va[j] = (R)m.a[j];
@@ -523,7 +564,7 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.tpb = tpb;
   a.ppt = ppt;
   a.chunks = P.chunks;
-  a.tab_stride = D < 3 ? 3 : D;
+  a.tab_stride = (m.vol_kind == 1 || m.vol_kind == 2) ? 2 * D : (D < 3 ? 3 : D);
   a.payoff = m.payoff;
   a.obstacle = m.obstacle;
   a.absflag = (m.vol_kind == 1) ? 1 : 0;
@@ -547,17 +588,22 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
     else
       a.alpha = reinterpret_cast<const R*>(P.beta);
   }
-  const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense);
+  const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense, a.tab_stride);
   const int vk = (m.vol_kind == 0) ? VK_CONST : (m.vol_kind == 3) ? VK_DUPIRE : VK_TANH;
   const unsigned grid = (unsigned)P.n * (unsigned)P.chunks;
-  if (dense) {
-    if (vk == VK_CONST) return launch_one<VK_CONST, EV_DENSE3>(a, grid, tpb, smem, st);
-    if (vk == VK_TANH) return launch_one<VK_TANH, EV_DENSE3>(a, grid, tpb, smem, st);
-    return launch_one<VK_DUPIRE, EV_DENSE3>(a, grid, tpb, smem, st);
+  if (dense) {  // the dense evaluation implies a constant correlation
+    if (vk == VK_CONST) return launch_one<VK_CONST, EV_DENSE3, true>(a, grid, tpb, smem, st);
+    if (vk == VK_TANH) return launch_one<VK_TANH, EV_DENSE3, true>(a, grid, tpb, smem, st);
+    return launch_one<VK_DUPIRE, EV_DENSE3, true>(a, grid, tpb, smem, st);
   }
-  if (vk == VK_CONST) return launch_one<VK_CONST, EV_TABLES>(a, grid, tpb, smem, st);
-  if (vk == VK_TANH) return launch_one<VK_TANH, EV_TABLES>(a, grid, tpb, smem, st);
-  return launch_one<VK_DUPIRE, EV_TABLES>(a, grid, tpb, smem, st);
+  if (cc) {
+    if (vk == VK_CONST) return launch_one<VK_CONST, EV_TABLES, true>(a, grid, tpb, smem, st);
+    if (vk == VK_TANH) return launch_one<VK_TANH, EV_TABLES, true>(a, grid, tpb, smem, st);
+    return launch_one<VK_DUPIRE, EV_TABLES, true>(a, grid, tpb, smem, st);
+  }
+  if (vk == VK_CONST) return launch_one<VK_CONST, EV_TABLES, false>(a, grid, tpb, smem, st);
+  if (vk == VK_TANH) return launch_one<VK_TANH, EV_TABLES, false>(a, grid, tpb, smem, st);
+  return launch_one<VK_DUPIRE, EV_TABLES, false>(a, grid, tpb, smem, st);
 }
 
 }  // namespace paths
