@@ -198,6 +198,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
+    time.sleep(1.0)  # let nvidia-smi start before the timed region
     reps = []
     if world > 1:
         torch.distributed.barrier()

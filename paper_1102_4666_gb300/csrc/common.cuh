@@ -139,7 +139,8 @@ struct ProblemDev {
   double* rhs = nullptr;      // [p]
   double* delta = nullptr;    // [p] solution of the normal equations
   double* res = nullptr;      // [p] refinement residual
-  double* v = nullptr;        // [n] B delta
+  double* v = nullptr;        // [max(n, p)] B delta; original diagonal during Cholesky
+  double* dinv = nullptr;     // [p] reciprocal diagonal of the Cholesky factor
   double* alpha = nullptr;    // [p] coefficients (FP64 master)
   float* alpha32 = nullptr;   // [p] FP32 copy for the mixed path kernel
   uint2* pairs = nullptr;     // [p] packed (variate, degree) bytes

@@ -97,54 +97,66 @@ __global__ void k_save_diag(const double* __restrict__ A, int p, double* __restr
 }
 
 // Right-looking blocked Cholesky, panel width 32, lower factor in place.
-// Panel step 1: one CTA factors the 32x32 diagonal block in shared memory.
-// A pivot below 1e-13 of its original diagonal entry (or not finite) marks
-// the matrix as numerically singular: ST_NOT_PD, and the pivot becomes NaN.
-__global__ void __launch_bounds__(256) k_chol_diag(double* __restrict__ A, int p, int j0,
-                                                   int* __restrict__ status,
-                                                   const double* __restrict__ diag0) {
+// Panel step 1: one warp factors the 32x32 diagonal block in shared memory
+// and stores the reciprocals of its diagonal in dinv.  A pivot below 1e-13
+// of its original diagonal entry (or not finite) marks the matrix as
+// numerically singular: ST_NOT_PD, and the pivot becomes NaN.
+__global__ void __launch_bounds__(32) k_chol_diag(double* __restrict__ A, int p, int j0,
+                                                  int* __restrict__ status,
+                                                  const double* __restrict__ diag0,
+                                                  double* __restrict__ dinv) {
   __shared__ double Dg[32][33];
   const int nb = min(32, p - j0);
-  const int tid = threadIdx.x;
-  for (int q = tid; q < 32 * 32; q += 256) {
+  const int lane = threadIdx.x;
+  for (int q = lane; q < 32 * 32; q += 32) {
     const int r = q >> 5, c = q & 31;
     Dg[r][c] = (r < nb && c < nb && c <= r) ? A[(size_t)(j0 + r) * p + (j0 + c)] : 0.0;
   }
-  __syncthreads();
+  __syncwarp();
   for (int c = 0; c < nb; ++c) {
-    if (tid == 0) {
+    double inv = 0.0;
+    if (lane == 0) {
       const double piv = Dg[c][c];
       if (!(piv > 1e-13 * diag0[j0 + c]) || !isfinite(piv)) {
         atomicOr(status, ST_NOT_PD);
         Dg[c][c] = nan("");
+        inv = nan("");
       } else {
-        Dg[c][c] = sqrt(piv);
+        const double dcc = sqrt(piv);
+        Dg[c][c] = dcc;
+        inv = 1.0 / dcc;
       }
+      dinv[j0 + c] = inv;
     }
-    __syncthreads();
-    if (tid > c && tid < nb) Dg[tid][c] /= Dg[c][c];
-    __syncthreads();
-    for (int q = tid; q < 32 * 32; q += 256) {
-      const int r = q >> 5, s2 = q & 31;
-      if (s2 > c && r >= s2 && r < nb) Dg[r][s2] -= Dg[r][c] * Dg[s2][c];
+    inv = __shfl_sync(0xffffffffu, inv, 0);
+    __syncwarp();
+    if (lane > c && lane < nb) Dg[lane][c] *= inv;
+    __syncwarp();
+    // rank-1 update of the trailing block: lane handles row r = lane
+    if (lane > c && lane < nb) {
+      const double lrc = Dg[lane][c];
+      for (int s2 = c + 1; s2 <= lane; ++s2) Dg[lane][s2] -= lrc * Dg[s2][c];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int q = tid; q < 32 * 32; q += 256) {
+  for (int q = lane; q < 32 * 32; q += 32) {
     const int r = q >> 5, c = q & 31;
     if (r < nb && c <= r) A[(size_t)(j0 + r) * p + (j0 + c)] = Dg[r][c];
   }
 }
 
 // Panel step 2: rows below the diagonal block solve x L_jj^T = a (forward
-// substitution), one thread per row.
-__global__ void __launch_bounds__(32) k_chol_trsm(double* __restrict__ A, int p, int j0) {
+// substitution with the reciprocal diagonal), one thread per row.
+__global__ void __launch_bounds__(32) k_chol_trsm(double* __restrict__ A, int p, int j0,
+                                                  const double* __restrict__ dinv) {
   __shared__ double Dg[32][33];
+  __shared__ double di[32];
   const int nb = min(32, p - j0);
   for (int q = threadIdx.x; q < 32 * 32; q += 32) {
     const int r = q >> 5, c = q & 31;
     Dg[r][c] = (r < nb && c < nb && c <= r) ? A[(size_t)(j0 + r) * p + (j0 + c)] : 0.0;
   }
+  di[threadIdx.x] = threadIdx.x < nb ? dinv[j0 + threadIdx.x] : 0.0;
   __syncthreads();
   const int row = j0 + nb + 32 * blockIdx.x + threadIdx.x;
   if (row >= p) return;
@@ -157,7 +169,7 @@ __global__ void __launch_bounds__(32) k_chol_trsm(double* __restrict__ A, int p,
       double acc = xr[c];
 #pragma unroll
       for (int q = 0; q < c; ++q) acc -= xr[q] * Dg[c][q];
-      xr[c] = acc / Dg[c][c];
+      xr[c] = acc * di[c];
     }
   }
 #pragma unroll
@@ -200,37 +212,60 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ A, int
   }
 }
 
-// x (+)= A^{-1} b with the Cholesky factor in the lower triangle of A:
-// forward then backward substitution, column-oriented, one CTA.
-__global__ void __launch_bounds__(1024) k_chol_solve(const double* __restrict__ A, int p,
-                                                     const double* __restrict__ b,
-                                                     double* __restrict__ x, int accumulate,
-                                                     double* __restrict__ work) {
-  const int tid = threadIdx.x;
-  for (int r = tid; r < p; r += blockDim.x) work[r] = b[r];
+// x (+)= A^{-1} b with the Cholesky factor L in the lower triangle of A and
+// its reciprocal diagonal in dinv: L y = b, then L^T x = y, by blocks of 32.
+// Warp 0 solves each 32x32 diagonal block with shuffles; all threads then
+// update the rest of the vector with that block's 32 columns (forward: a
+// row segment per thread; backward: coalesced column reads).  One CTA.
+__global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ A, int p,
+                                                    const double* __restrict__ dinv,
+                                                    const double* __restrict__ b,
+                                                    double* __restrict__ x, int accumulate) {
+  extern __shared__ double yv[];  // p
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int r = tid; r < p; r += blockDim.x) yv[r] = b[r];
   __syncthreads();
-  __shared__ double piv;
-  for (int c = 0; c < p; ++c) {
-    if (tid == 0) {
-      work[c] /= A[(size_t)c * p + c];
-      piv = work[c];
+  const int nblk = (p + 31) / 32;
+  for (int blk = 0; blk < nblk; ++blk) {
+    const int c0 = blk * 32, nb = min(32, p - c0);
+    if (warp == 0) {
+      double yi = lane < nb ? yv[c0 + lane] : 0.0;
+      for (int c = 0; c < nb; ++c) {
+        if (lane == c) yi *= dinv[c0 + c];
+        const double yc = __shfl_sync(0xffffffffu, yi, c);
+        if (lane > c && lane < nb) yi -= A[(size_t)(c0 + lane) * p + c0 + c] * yc;
+      }
+      if (lane < nb) yv[c0 + lane] = yi;
     }
     __syncthreads();
-    const double yc = piv;
-    for (int r = c + 1 + tid; r < p; r += blockDim.x) work[r] -= A[(size_t)r * p + c] * yc;
-    __syncthreads();
-  }
-  for (int c = p - 1; c >= 0; --c) {
-    if (tid == 0) {
-      work[c] /= A[(size_t)c * p + c];
-      piv = work[c];
+    for (int r = c0 + nb + tid; r < p; r += blockDim.x) {
+      const double* row = A + (size_t)r * p + c0;
+      double acc = 0.0;
+      for (int c = 0; c < nb; ++c) acc += row[c] * yv[c0 + c];
+      yv[r] -= acc;
     }
     __syncthreads();
-    const double xc = piv;
-    for (int r = tid; r < c; r += blockDim.x) work[r] -= A[(size_t)c * p + r] * xc;
+  }
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int c0 = blk * 32, nb = min(32, p - c0);
+    if (warp == 0) {
+      double xi = lane < nb ? yv[c0 + lane] : 0.0;
+      for (int c = nb - 1; c >= 0; --c) {
+        if (lane == c) xi *= dinv[c0 + c];
+        const double xc = __shfl_sync(0xffffffffu, xi, c);
+        if (lane < c) xi -= A[(size_t)(c0 + c) * p + c0 + lane] * xc;
+      }
+      if (lane < nb) yv[c0 + lane] = xi;
+    }
+    __syncthreads();
+    for (int r = tid; r < c0; r += blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c < nb; ++c) acc += A[(size_t)(c0 + c) * p + r] * yv[c0 + c];
+      yv[r] -= acc;
+    }
     __syncthreads();
   }
-  for (int r = tid; r < p; r += blockDim.x) x[r] = accumulate ? (x[r] + work[r]) : work[r];
+  for (int r = tid; r < p; r += blockDim.x) x[r] = accumulate ? (x[r] + yv[r]) : yv[r];
 }
 
 // alpha += delta; ||delta||_2, ||delta||_inf into the report block; FP32 copy
@@ -380,10 +415,10 @@ void launch_cholesky(const ProblemDev& P, cudaStream_t st) {
   // P.v (n >= p entries) holds the original diagonal during the factorisation
   k_save_diag<<<(P.p + 255) / 256, 256, 0, st>>>(P.A, P.p, P.v);
   for (int j0 = 0; j0 < P.p; j0 += 32) {
-    k_chol_diag<<<1, 256, 0, st>>>(P.A, P.p, j0, P.status, P.v);
+    k_chol_diag<<<1, 32, 0, st>>>(P.A, P.p, j0, P.status, P.v, P.dinv);
     const int m = P.p - j0 - 32;
     if (m > 0) {
-      k_chol_trsm<<<(m + 31) / 32, 32, 0, st>>>(P.A, P.p, j0);
+      k_chol_trsm<<<(m + 31) / 32, 32, 0, st>>>(P.A, P.p, j0, P.dinv);
       const int T = (m + 31) / 32;
       k_chol_update<<<T * (T + 1) / 2, 256, 0, st>>>(P.A, P.p, j0);
     }
@@ -391,9 +426,11 @@ void launch_cholesky(const ProblemDev& P, cudaStream_t st) {
 }
 
 void launch_chol_solve(const ProblemDev& P, const double* b, double* x, cudaStream_t st) {
-  // work vector: the residual buffer is free at this point when b != res;
-  // use v (n >= p) as scratch
-  k_chol_solve<<<1, 1024, 0, st>>>(P.A, P.p, b, x, b == P.res ? 1 : 0, P.v);
+  // the refinement solve (b == res) adds its correction to x
+  const size_t smem = (size_t)P.p * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_chol_solve<<<1, 256, smem, st>>>(P.A, P.p, P.dinv, b, x, b == P.res ? 1 : 0);
 }
 
 void launch_refine_residual(const ProblemDev& P, cudaStream_t st) {

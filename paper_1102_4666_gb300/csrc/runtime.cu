@@ -180,7 +180,7 @@ size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int t
   add((size_t)n * chunks * 8);
   add((size_t)n * 8);
   add((size_t)p * p * 8);
-  add((size_t)p * 8 * 3);
+  add((size_t)p * 8 * 4);
   add((size_t)(n > p ? n : p) * 8);
   add((size_t)p * 8);
   add((size_t)p * 4);
@@ -337,9 +337,10 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     P.partial = (double*)take((size_t)n * s.chunks * 8);
     P.c = (double*)take((size_t)n * 8);
     P.A = (double*)take((size_t)p * p * 8);
-    P.rhs = (double*)take((size_t)p * 8 * 3);
+    P.rhs = (double*)take((size_t)p * 8 * 4);
     P.delta = P.rhs + p;
     P.res = P.rhs + 2 * p;
+    P.dinv = P.rhs + 3 * p;
     P.v = (double*)take((size_t)(n > p ? n : p) * 8);  // also Cholesky scratch (p)
     P.alpha = (double*)take((size_t)p * 8);
     P.alpha32 = (float*)take((size_t)p * 4);

@@ -129,8 +129,12 @@ def _alpha(cfg, nu, scale=2.0, seed=3):
 
 
 def _scale(cfg, nu, alpha, t, x):
+    """Scale of the integrand a_m = (T - t)(-r u + lambda (Phi - u)^+ + d_t u + L u)
+    + Phi - u (eq. psiN with the driver of eq. bsde-penal-2): both u and the
+    payoff Phi enter multiplied by up to 1 + lambda T."""
     u = O.basis_matrix(cfg, nu, t, x) @ alpha
-    return max(1.0, cfg["K"] * 0.5, np.max(np.abs(u)) * (1.0 + cfg["lambda"] * cfg["T"]))
+    phi_max = max(cfg["K"], float(np.dot(cfg["weights"], np.exp(cfg["hi"][1:]))))
+    return max(1.0, phi_max, np.max(np.abs(u))) * (1.0 + cfg["lambda"] * cfg["T"])
 
 
 # (case, eval_mode): 0 automatic (dense monomial form for total degree <= 3
