@@ -172,6 +172,53 @@ def run_profile_case(args):
     return 0
 
 
+def run_serving(n_requests, precision="mixed", slots=16, seed=7, load=0.8):
+    """Continuous-batching serving mix: a seeded Poisson stream of pricing
+    requests of uneven d, n, M and degree (workloads.serving_mix) submitted
+    at their arrival times to bsde_server; arrival rate calibrated to `load`
+    times the measured capacity.  Returns p50/p99 latency and throughput."""
+    import paper_1102_4666_gb300 as G
+    reqs = workloads.serving_mix(n_requests, seed=seed)
+    mean_steps = sum(workloads.path_steps(r) for r in reqs) / len(reqs)
+    # capacity: a few requests back to back on a warm server
+    srv = G.Server(max_slots=slots, precision=precision)
+    calib = reqs[:min(16, len(reqs))]
+    t0 = time.perf_counter()
+    ids = [srv.submit(r) for r in calib]
+    srv.drain()
+    el = time.perf_counter() - t0
+    for i in ids:
+        srv.poll(i)
+    cap = sum(workloads.path_steps(r) for r in calib) / el
+    srv.close()
+    rate = load * cap / mean_steps
+    rng = __import__("random").Random(seed)
+    srv = G.Server(max_slots=slots, precision=precision)
+    t_start = time.perf_counter()
+    t_arr = 0.0
+    ids = []
+    for r in reqs:
+        t_arr += rng.expovariate(rate)
+        now = time.perf_counter() - t_start
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        ids.append(srv.submit(r))
+    srv.drain()
+    wall = time.perf_counter() - t_start
+    st = srv.stats()
+    bad = 0
+    for i in ids:
+        rep = srv.poll(i)
+        if rep is None or rep.status != 0:
+            bad += 1
+    srv.close()
+    return {"requests": len(reqs), "precision": precision, "slots": slots,
+            "arrival_rate_hz": rate, "calibrated_capacity_path_steps_per_s": cap, "load": load,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "path_steps_per_s": st["path_steps"] / wall, "busy_path_steps_per_s": st["path_steps_per_s"],
+            "wall_s": wall, "failed": bad}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -264,6 +311,7 @@ def run_ours(args):
     launch_steps = cfg["n"] * cfg["M"] * cfg["N"]
     achieved = FLOPS_PER_PATH_STEP * launch_steps / (path_ms * 1e-3) / 1e12 if path_ms > 0 else None
     cpu = cpu_oracle_rate(cfg, budget_s=args.cpu_budget) if not args.no_cpu else None
+    serving = run_serving(args.serving_requests) if args.serving_requests > 0 else None
     rep0 = reps[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -286,6 +334,7 @@ def run_ours(args):
         "solve": {"price": rep0.price, "delta0": rep0.delta[0], "ms_paths": rep0.ms_paths,
                   "ms_gram": rep0.ms_gram, "ms_solve": rep0.ms_solve, "ms_total": rep0.ms_total},
         "cpu_baseline": cpu,
+        "serving": serving,
     }
     print(json.dumps(line))
     if world > 1:
@@ -303,6 +352,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--serving-requests", type=int, default=100,
+                    help="requests of the Poisson serving mix (0: skip; 2000: the full mix)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
     if args.case == "profile":

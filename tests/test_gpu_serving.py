@@ -1,0 +1,63 @@
+"""The continuous-batching server: each request's result is the same alone
+(a dedicated solver) and in the mix (admitted next to others, sharing the
+device), because every kernel reduces in a fixed order."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    reqs = []
+    base = workloads.serving_mix(8, seed=11)
+    for j, r in enumerate(base):
+        # keep the test short: small point sets and path counts
+        r["n"] = max(2 * workloads.basis_size(r["d"], r["eta"]) + 8, 200)
+        r["M"] = 300 + 50 * j
+        r["K_it"] = 3
+        reqs.append(r)
+    return reqs
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_alone_equals_in_the_mix(precision):
+    import paper_1102_4666_gb300 as G
+    reqs = _mix()
+    alone = []
+    for r in reqs:
+        s = G.Solver(r, precision=precision)
+        rep = s.solve(use_graph=1)
+        alone.append((rep.price, list(rep.delta[:r["d"]]), rep.status))
+        s.close()
+    srv = G.Server(max_slots=4, precision=precision)
+    ids = [srv.submit(r) for r in reqs]
+    assert srv.drain(120000.0) == G.OK
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["queued"] == 0 and st["running"] == 0
+    for r, rid, (p, d, stt) in zip(reqs, ids, alone):
+        rep = srv.poll(rid)
+        assert rep is not None and rep.status == stt == G.OK
+        assert rep.price == p
+        assert list(rep.delta[:r["d"]]) == d
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    srv.close()
+
+
+def test_admission_by_memory_budget():
+    """With a budget that fits one request at a time, requests still all
+    complete (queued until memory frees up); a request larger than the
+    whole budget is refused at submit."""
+    import paper_1102_4666_gb300 as G
+    reqs = [r for r in _mix() if workloads.basis_size(r["d"], r["eta"]) <= 400][:4]
+    srv = G.Server(max_slots=4, mem_budget=64 << 20, precision="mixed")
+    ids = [srv.submit(r) for r in reqs]
+    assert srv.drain(120000.0) == G.OK
+    for rid in ids:
+        rep = srv.poll(rid)
+        assert rep is not None and rep.status == G.OK
+    big = workloads.config("c4", eta=4)  # p = 1365: about 120 MB resident
+    with pytest.raises(G.BsdeError):
+        srv.submit(big)
+    srv.close()
