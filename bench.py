@@ -43,6 +43,25 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_seed(base_seed, rank):
+    """Seed of the independent problem that rank `rank` solves."""
+    return base_seed + 1000 * rank
+
+
+def weak_scaling_value(ms_local, steps, units_per_step, device=None):
+    """Whole-job throughput under weak scaling: every rank solves its own
+    problems, the job time is the slowest rank's.  Returns (value, ms_max)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = float(ms_local)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * steps * units_per_step / (ms * 1e-3), ms
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
 
@@ -232,7 +251,7 @@ def run_ours(args):
     import paper_1102_4666_gb300 as G
 
     cfg = workloads.config(CONFIG)
-    cfg["seed"] = cfg["seed"] + 1000 * rank  # independent problem per rank
+    cfg["seed"] = rank_seed(cfg["seed"], rank)  # independent problem per rank
     stream = torch.cuda.Stream(device=dev)
     s = G.Solver(cfg, precision="mixed", device=local, stream=stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -263,12 +282,8 @@ def run_ours(args):
         torch.distributed.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     steps_per_solve = workloads.path_steps(cfg)
-    value = world * args.steps * steps_per_solve / (ms * 1e-3)
+    value, ms = weak_scaling_value(ms, args.steps, steps_per_solve, device=dev)
     launches = sum(r.kernel_launches for r in reps)
     path_ms = sum(r.ms_paths for r in reps) / max(1, sum(r.path_launches for r in reps))
 

@@ -60,6 +60,7 @@ struct bsde_server {
   std::map<uint64_t, std::unique_ptr<Req>> done;
   std::vector<cudaStream_t> free_streams;
   size_t used_bytes = 0;
+  int admitting = 0;  // popped from the queue, not yet in running/done
   std::vector<double> latencies_ms;
   double path_steps = 0.0, busy_s = 0.0, busy_since = -1.0;
   uint64_t completed = 0;
@@ -85,6 +86,7 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   }
   req->stream = st;
+  ++admitting;
   lk.unlock();
   // device work outside the lock: allocation, capture, graph launch
   req->prob.reset(new Problem());
@@ -97,6 +99,7 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
   cudaEventCreate(&req->e1);
   req->rc = P.start(req->prm, al, 0, st, req->e0, req->e1);
   lk.lock();
+  --admitting;
   if (req->rc != BSDE_OK) {
     // failed before reaching the device: complete immediately
     memset(&req->rep, 0, sizeof(req->rep));
@@ -153,7 +156,7 @@ void bsde_server::loop() {
       busy_since = -1.0;
     }
     if (!progressed) {
-      if (running.empty() && queue.empty())
+      if (running.empty() && queue.empty() && admitting == 0)
         cv.wait(lk);
       else
         cv.wait_for(lk, std::chrono::microseconds(200));
@@ -239,7 +242,7 @@ int bsde_server_poll(bsde_server* s, uint64_t id, bsde_report* rep) {
 int bsde_server_drain(bsde_server* s, double timeout_ms) {
   if (!s) return BSDE_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
-  auto pred = [s] { return s->queue.empty() && s->running.empty(); };
+  auto pred = [s] { return s->queue.empty() && s->running.empty() && s->admitting == 0; };
   if (timeout_ms > 0) {
     if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred))
       return BSDE_ERR_TIMEOUT;
