@@ -145,7 +145,8 @@ struct ProblemDev {
   float* alpha32 = nullptr;   // [p] FP32 copy for the mixed path kernel
   uint2* pairs = nullptr;     // [p] packed (variate, degree) bytes
   uint8_t* nnz = nullptr;     // [p] active variates per basis function
-  uint32_t* key = nullptr;    // [2] Philox key
+  uint32_t* key = nullptr;    // [2] Philox key (device copy, read by the points kernel)
+  uint32_t seed_key[2] = {0, 0};  // the same key on the host, a parameter of the path kernel
   int* status = nullptr;      // [1] device status bits
   double* out = nullptr;      // report block (see OUT_* offsets)
   // dense evaluation (basis of total degree <= 3): monomial coefficients

@@ -52,7 +52,7 @@ struct Args {
   R rho;  // constant correlation (dense evaluation)
   R kc[D];  // -2 log2(e) kappa_j: e^{2 (x - kappa)} = 2^{x 2 log2(e) + kc}
   uint32_t k;
-  const uint32_t* key;
+  uint32_t key0, key1;  // Philox key as kernel parameters: warp-uniform round keys
   const double* pt;
   const double* px;
   const R* alpha;
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
   for (int q = tid; q < DP * DP; q += tpb) s_cp[q] = (&a.Cp[0][0])[q];
   __syncthreads();
 
-  const Philox ph{a.key[0], a.key[1]};
+  const Philox ph{a.key0, a.key1};
   const uint32_t tagU = (TAG_U << 24) | a.k, tagZ = (TAG_Z << 24) | a.k, tagB = (TAG_B << 24) | a.k;
   constexpr int G = 4 / gcd_c(D, 4);  // steps per group: G*D normals = whole Philox blocks
   constexpr int NB = G * D / 4;
@@ -570,7 +570,8 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.absflag = (m.vol_kind == 1) ? 1 : 0;
   a.vol_sin = (m.vol_kind == 2) ? 1 : 0;
   a.k = k;
-  a.key = P.key;
+  a.key0 = P.seed_key[0];
+  a.key1 = P.seed_key[1];
   a.pt = P.t;
   a.px = P.x;
   if constexpr (sizeof(R) == 4)

@@ -146,6 +146,8 @@ extern "C" BSDE_API int bsde_corrections_noalloc(
     P.c = c_dev;
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    P.seed_key[0] = key[0];
+    P.seed_key[1] = key[1];
     // every scratch word the kernels read is rewritten here; the partial
     // sums are all overwritten by the path kernel before they are read
     e = cudaMemcpyAsync(P.key, key, sizeof(key), cudaMemcpyHostToDevice, st);

@@ -379,6 +379,8 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     e = cudaMemcpyAsync(dev.out + OUT_SIZE + 1 + BSDE_DMAX, logS0, (size_t)d * 8,
                         cudaMemcpyHostToDevice, st);
   uint32_t key[2] = {(uint32_t)(prm.seed & 0xffffffffu), (uint32_t)(prm.seed >> 32)};
+  dev.seed_key[0] = key[0];
+  dev.seed_key[1] = key[1];
   if (e == cudaSuccess) e = cudaMemcpyAsync(dev.key, key, 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dev.status, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // key/logS0 live on this stack
@@ -475,7 +477,8 @@ int Problem::start(const bsde_solve_params& prm, Allocator& al, size_t budget, c
     std::ostringstream os;
     os << shape.d << ' ' << shape.n << ' ' << shape.p << ' ' << shape.M << ' ' << shape.N << ' '
        << prm.K_it << ' ' << prm.k_start << ' ' << prm.refine_steps << ' ' << prm.timing << ' '
-       << mixed << ' ' << (void*)block;
+       << mixed << ' ' << (void*)block << ' ' << prm.seed << ' ' << prm.eval_mode << ' '
+       << prm.paths_tpb << ' ' << prm.paths_ppt;
     if (!gexec || os.str() != graph_key) {
       destroy_graph();
       cudaGraph_t graph = nullptr;
