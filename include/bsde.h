@@ -176,6 +176,12 @@ typedef struct {
                        32..256, a multiple of 32)                       */
   int paths_ppt;    /* paths per thread of the path kernel (0: automatic;
                        1..16)                                           */
+  int ls_mode;      /* least-squares refit (eq. alpha): 0 normal equations,
+                       tensor-core/FP64 Gram + FP64 Cholesky + refinement;
+                       1 FP64 Householder QR with column pivoting and rank
+                       truncation at 1e-13 |R_00| on the design matrix (the
+                       role of LAPACK dgelsy in Section 3.2.2; slower, for
+                       ill-conditioned or rank-deficient bases)        */
 } bsde_solve_params;
 
 typedef struct {
@@ -195,6 +201,8 @@ typedef struct {
   double path_steps_per_s;     /* path_steps / ms_total                     */
   int path_launches;           /* path-kernel launches in the solve          */
   int kernel_launches;         /* all kernel launches in the solve           */
+  int rank;                    /* numerical rank of the last refit (ls_mode 1;
+                                  p with ls_mode 0)                           */
 } bsde_report;
 
 /* Run Algorithm 2 for K_it iterations from alpha = 0 (or from the

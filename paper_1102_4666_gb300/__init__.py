@@ -69,7 +69,7 @@ class bsde_solve_params(ctypes.Structure):
                 ("K_it", ctypes.c_int), ("seed", ctypes.c_uint64), ("k_start", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("use_graph", ctypes.c_int), ("timing", ctypes.c_int),
                 ("allow_underdetermined", ctypes.c_int), ("eval_mode", ctypes.c_int),
-                ("paths_tpb", ctypes.c_int), ("paths_ppt", ctypes.c_int)]
+                ("paths_tpb", ctypes.c_int), ("paths_ppt", ctypes.c_int), ("ls_mode", ctypes.c_int)]
 
 
 class bsde_report(ctypes.Structure):
@@ -80,7 +80,7 @@ class bsde_report(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_paths", ctypes.c_double), ("ms_gram", ctypes.c_double),
                 ("ms_solve", ctypes.c_double), ("path_steps", ctypes.c_double),
                 ("path_steps_per_s", ctypes.c_double), ("path_launches", ctypes.c_int),
-                ("kernel_launches", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int), ("rank", ctypes.c_int)]
 
     def to_dict(self):
         d, K = self.d, self.K_it
@@ -90,7 +90,8 @@ class bsde_report(ctypes.Structure):
                 "resid_linf": list(self.resid_linf[:K]), "ms_total": self.ms_total,
                 "ms_paths": self.ms_paths, "ms_gram": self.ms_gram, "ms_solve": self.ms_solve,
                 "path_steps": self.path_steps, "path_steps_per_s": self.path_steps_per_s,
-                "path_launches": self.path_launches, "kernel_launches": self.kernel_launches}
+                "path_launches": self.path_launches, "kernel_launches": self.kernel_launches,
+                "rank": self.rank}
 
 
 class bsde_server_opts(ctypes.Structure):
@@ -235,7 +236,7 @@ def model_structs(cfg):
 
 
 def solve_params(cfg, seed=None, K_it=None, k_start=0, refine_steps=-1, use_graph=1, timing=0,
-                 allow_underdetermined=0, eval_mode=0, paths_tpb=0, paths_ppt=0):
+                 allow_underdetermined=0, eval_mode=0, paths_tpb=0, paths_ppt=0, ls_mode=0):
     p = bsde_solve_params()
     p.M, p.N_steps, p.eta, p.q = cfg["M"], cfg["N"], cfg["eta"], cfg.get("q", 1.0)
     p.K_it = cfg["K_it"] if K_it is None else K_it
@@ -244,6 +245,7 @@ def solve_params(cfg, seed=None, K_it=None, k_start=0, refine_steps=-1, use_grap
     p.allow_underdetermined = allow_underdetermined
     p.eval_mode = eval_mode
     p.paths_tpb, p.paths_ppt = paths_tpb, paths_ppt
+    p.ls_mode = ls_mode
     return p
 
 

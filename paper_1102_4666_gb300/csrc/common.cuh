@@ -157,6 +157,13 @@ struct ProblemDev {
   int* conv_row = nullptr;    // [pm + 1] CSR rows of the Chebyshev -> monomial map
   int* conv_l = nullptr;      // basis-function index of each entry
   double* conv_c = nullptr;   // coefficient of each entry
+  // pivoted-QR refit workspace (ls_mode 1)
+  double* qr_W = nullptr;     // [p][n_pad] design matrix, then R and the reflectors
+  double* qr_y = nullptr;     // [n] right-hand side, then Q^T c
+  double* qr_nrm = nullptr;   // [p] squared norms of the remaining columns
+  double* qr_tau = nullptr;   // [p] reflector coefficients
+  int* qr_perm = nullptr;     // [p] column permutation
+  int* qr_rank = nullptr;     // [1] numerical rank
 };
 
 // offsets in ProblemDev::out
@@ -196,4 +203,5 @@ void launch_eval_points(const ModelHost& m, const GridHost& g, const ProblemDev&
                         cudaStream_t st);
 size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed, bool dense);
 void launch_cheb2mono(const ProblemDev& P, cudaStream_t st);
+void launch_qr_solve(const ProblemDev& P, cudaStream_t st);
 int paths_supported_d(int d);

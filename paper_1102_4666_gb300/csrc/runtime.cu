@@ -158,7 +158,7 @@ int Problem::choose_launch(int d, int p, int eta, int N, int M, bool mx, bool de
 }
 
 size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int tpb, int ppt, int pm,
-                               int conv_nnz) {
+                               int conv_nnz, bool qr) {
   (void)N;
   const int n_pad = (n + 31) / 32 * 32;
   const int p_pad = (p + 127) / 128 * 128;
@@ -194,6 +194,12 @@ size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int t
     add((size_t)(pm + 1) * 4);
     add((size_t)conv_nnz * 4);
     add((size_t)conv_nnz * 8);
+  }
+  if (qr) {
+    add((size_t)p * n_pad * 8);
+    add((size_t)n * 8);
+    add((size_t)p * 8 * 2);
+    add((size_t)p * 4 + 16);
   }
   return b;
 }
@@ -263,6 +269,11 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     return BSDE_ERR_INVALID_ARG;
   }
   s.dense = pm > 0 && const_corr && prm.eval_mode != 1;
+  if (prm.ls_mode != 0 && prm.ls_mode != 1) {
+    err = "solve: ls_mode must be 0 (normal equations) or 1 (pivoted QR)";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  s.qr = prm.ls_mode == 1;
   s.pm = s.dense ? pm : 0;
   if (choose_launch(d, s.dense ? pm : p, s.eta, s.N, s.M, mixed, s.dense, s.tpb, s.ppt) != BSDE_OK) {
     err = "solve: basis and step count too large for the shared-memory tables";
@@ -286,7 +297,7 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   s.chunks = (s.M + s.tpb * s.ppt - 1) / (s.tpb * s.ppt);
   if (!block || !(s == alloc_shape)) {
     const size_t need = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt, s.pm,
-                                       s.dense ? (int)conv_l.size() : 0);
+                                       s.dense ? (int)conv_l.size() : 0, s.qr);
     if (budget && need > budget) {
       std::ostringstream os;
       os << "solve: needs " << need << " bytes of device memory, budget " << budget;
@@ -358,6 +369,14 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
       P.conv_l = (int*)take(conv_l.size() * 4);
       P.conv_c = (double*)take(conv_c.size() * 8);
     }
+    if (s.qr) {
+      P.qr_W = (double*)take((size_t)p * s.n_pad * 8);
+      P.qr_y = (double*)take((size_t)n * 8);
+      P.qr_nrm = (double*)take((size_t)p * 8 * 2);
+      P.qr_tau = P.qr_nrm + p;
+      P.qr_perm = (int*)take((size_t)p * 4 + 16);
+      P.qr_rank = P.qr_perm + p;
+    }
     dev = P;
     coeffs_valid = false;
   }
@@ -417,24 +436,31 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
   if (rec) record(ev[1], st);
   launch_reduce_c(dev, shape.M, st);
   if (rec) record(ev[2], st);
-  if (mixed) {
-    e = launch_gram_tc(dev, st);
-    if (e != cudaSuccess) {
-      err = std::string("tensor-core Gram launch failed: ") + cudaGetErrorString(e);
-      return BSDE_ERR_CUDA;
-    }
+  if (shape.qr) {
+    // refit by pivoted QR on the design matrix (FP64)
+    if (rec) record(ev[3], st);
+    if (rec) record(ev[4], st);
+    launch_qr_solve(dev, st);
   } else {
-    launch_gram_f64(dev, st);
-  }
-  if (rec) record(ev[3], st);
-  launch_rhs(dev, st);
-  if (rec) record(ev[4], st);
-  launch_cholesky(dev, st);
-  launch_chol_solve(dev, dev.rhs, dev.delta, st);
-  const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 0);
-  for (int r = 0; r < refine; ++r) {
-    launch_refine_residual(dev, st);
-    launch_chol_solve(dev, dev.res, dev.delta, st);
+    if (mixed) {
+      e = launch_gram_tc(dev, st);
+      if (e != cudaSuccess) {
+        err = std::string("tensor-core Gram launch failed: ") + cudaGetErrorString(e);
+        return BSDE_ERR_CUDA;
+      }
+    } else {
+      launch_gram_f64(dev, st);
+    }
+    if (rec) record(ev[3], st);
+    launch_rhs(dev, st);
+    if (rec) record(ev[4], st);
+    launch_cholesky(dev, st);
+    launch_chol_solve(dev, dev.rhs, dev.delta, st);
+    const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 0);
+    for (int r = 0; r < refine; ++r) {
+      launch_refine_residual(dev, st);
+      launch_chol_solve(dev, dev.res, dev.delta, st);
+    }
   }
   if (rec) record(ev[5], st);
   launch_update(dev, k - prm.k_start, st);
@@ -478,7 +504,7 @@ int Problem::start(const bsde_solve_params& prm, Allocator& al, size_t budget, c
     os << shape.d << ' ' << shape.n << ' ' << shape.p << ' ' << shape.M << ' ' << shape.N << ' '
        << prm.K_it << ' ' << prm.k_start << ' ' << prm.refine_steps << ' ' << prm.timing << ' '
        << mixed << ' ' << (void*)block << ' ' << prm.seed << ' ' << prm.eval_mode << ' '
-       << prm.paths_tpb << ' ' << prm.paths_ppt;
+       << prm.paths_tpb << ' ' << prm.paths_ppt << ' ' << prm.ls_mode;
     if (!gexec || os.str() != graph_key) {
       destroy_graph();
       cudaGraph_t graph = nullptr;
@@ -546,9 +572,11 @@ int Problem::solve(const bsde_solve_params& prm, Allocator& al, size_t budget, c
 int Problem::finish_report(const bsde_solve_params& prm, cudaStream_t st, bsde_report* rep,
                            float ms_total) {
   std::vector<double> out(OUT_SIZE);
-  int status = 0;
+  int status = 0, rank = shape.p;
   cudaError_t e = cudaMemcpyAsync(out.data(), dev.out, OUT_SIZE * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, dev.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && shape.qr)
+    e = cudaMemcpyAsync(&rank, dev.qr_rank, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     err = std::string("solve: report copy failed: ") + cudaGetErrorString(e);
@@ -583,11 +611,13 @@ int Problem::finish_report(const bsde_solve_params& prm, cudaStream_t st, bsde_r
     r.path_steps = (double)prm.K_it * shape.n * (double)shape.M * shape.N;
     r.path_steps_per_s = ms_total > 0 ? r.path_steps / (ms_total * 1e-3) : 0.0;
     r.path_launches = prm.K_it;
+    r.rank = rank;
     const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 0);
     const int panels = (shape.p + 31) / 32;
     const int chol = 1 + 3 * panels - 2;
-    r.kernel_launches =
-        prm.K_it * (2 + (dev.dense ? 1 : 0) + 1 + 1 + (mixed ? 2 : 1) + 1 + chol + 1 + refine * 3 + 1 + 3);
+    const int steps_qr = shape.p < shape.n ? shape.p : shape.n;
+    const int refit = shape.qr ? (2 + 2 * steps_qr) : ((mixed ? 2 : 1) + 1 + chol + 1 + refine * 3);
+    r.kernel_launches = prm.K_it * (2 + (dev.dense ? 1 : 0) + 1 + 1 + refit + 1 + 3);
     // points, basis, paths, reduce, Gram (+ reduce), rhs, Cholesky, solve,
     // refinement (2 GEMVs + solve each), update, read-out (3)
     if (prm.timing && (int)events.size() >= 6 * prm.K_it) {

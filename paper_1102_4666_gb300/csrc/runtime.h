@@ -22,10 +22,11 @@ struct Allocator {
 struct Shape {
   int d = 0, n = 0, n_pad = 0, p = 0, p_pad = 0, eta = 0, M = 0, N = 0;
   int chunks = 0, tpb = 0, ppt = 0, splits = 0, pm = 0;
-  bool mixed = false, dense = false;
+  bool mixed = false, dense = false, qr = false;
   bool operator==(const Shape& o) const {
     return d == o.d && n == o.n && p == o.p && eta == o.eta && M == o.M && N == o.N &&
-           tpb == o.tpb && ppt == o.ppt && mixed == o.mixed && dense == o.dense && pm == o.pm;
+           tpb == o.tpb && ppt == o.ppt && mixed == o.mixed && dense == o.dense && pm == o.pm &&
+           qr == o.qr;
   }
 };
 
@@ -68,7 +69,7 @@ class Problem {
   void destroy_graph();  // after a model or grid change
   size_t bytes() const { return block_bytes; }
   static size_t estimate_bytes(int d, int n, int p, int M, int N, bool mixed, int tpb, int ppt,
-                               int pm = 0, int conv_nnz = 0);
+                               int pm = 0, int conv_nnz = 0, bool qr = false);
 
  private:
   void* block = nullptr;
