@@ -195,8 +195,12 @@ typedef struct {
   double resid_linf[BSDE_MAX_IT];  /* ||alpha^{k+1} - alpha^k||_inf         */
   double ms_total;             /* device time of the whole solve (events)   */
   double ms_paths;             /* device time of the path kernels (timing=1) */
-  double ms_gram;              /* device time of the Gram kernels (timing=1) */
-  double ms_solve;             /* device time of Cholesky + refinement       */
+  double ms_gram;              /* device time of the Gram matrix, its Cholesky
+                                  factor and inverse (timing=1; on a side
+                                  stream, overlapped with the path kernel)   */
+  double ms_solve;             /* device time of the refit after the paths
+                                  (RHS, inverse products, refinement; the
+                                  whole pivoted-QR refit with ls_mode 1)     */
   double path_steps;           /* K_it * n * M * N                          */
   double path_steps_per_s;     /* path_steps / ms_total                     */
   int path_launches;           /* path-kernel launches in the solve          */

@@ -141,6 +141,7 @@ struct ProblemDev {
   double* res = nullptr;      // [p] refinement residual
   double* v = nullptr;        // [max(n, p)] B delta; original diagonal during Cholesky
   double* dinv = nullptr;     // [p] reciprocal diagonal of the Cholesky factor
+  double* Ainv = nullptr;     // [p][p] inverse of the Gram matrix (overlapped refit)
   double* alpha = nullptr;    // [p] coefficients (FP64 master)
   float* alpha32 = nullptr;   // [p] FP32 copy for the mixed path kernel
   uint2* pairs = nullptr;     // [p] packed (variate, degree) bytes
@@ -204,4 +205,6 @@ void launch_eval_points(const ModelHost& m, const GridHost& g, const ProblemDev&
 size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed, bool dense);
 void launch_cheb2mono(const ProblemDev& P, cudaStream_t st);
 void launch_qr_solve(const ProblemDev& P, cudaStream_t st);
+void launch_inverse(const ProblemDev& P, cudaStream_t st);
+void launch_inv_gemv(const ProblemDev& P, const double* b, double* x, int accumulate, cudaStream_t st);
 int paths_supported_d(int d);

@@ -217,13 +217,16 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ A, int
 // Warp 0 solves each 32x32 diagonal block with shuffles; all threads then
 // update the rest of the vector with that block's 32 columns (forward: a
 // row segment per thread; backward: coalesced column reads).  One CTA.
+// With b == nullptr, CTA j solves A x = e_j and writes column j of A^{-1}
+// to x + j p (the inverse used by the overlapped refit).
 __global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ A, int p,
                                                     const double* __restrict__ dinv,
                                                     const double* __restrict__ b,
                                                     double* __restrict__ x, int accumulate) {
   extern __shared__ double yv[];  // p
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int r = tid; r < p; r += blockDim.x) yv[r] = b[r];
+  if (b == nullptr) x += (size_t)blockIdx.x * p;
+  for (int r = tid; r < p; r += blockDim.x) yv[r] = b ? b[r] : (r == (int)blockIdx.x ? 1.0 : 0.0);
   __syncthreads();
   const int nblk = (p + 31) / 32;
   for (int blk = 0; blk < nblk; ++blk) {
@@ -391,7 +394,33 @@ __global__ void k_cheb2mono(int pm, const int* __restrict__ row, const int* __re
   beta32[m] = (float)s;
 }
 
+// x (+)= Ainv b: warp per row, fixed shuffle order
+__global__ void k_inv_gemv(int p, const double* __restrict__ Ainv, const double* __restrict__ b,
+                           double* __restrict__ x, int accumulate) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= p) return;
+  const double* a = Ainv + (size_t)row * p;
+  double s = 0.0;
+  for (int c = lane; c < p; c += 32) s += a[c] * b[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = accumulate ? x[row] + s : s;
+}
+
 }  // namespace
+
+void launch_inverse(const ProblemDev& P, cudaStream_t st) {
+  const size_t smem = (size_t)P.p * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_chol_solve<<<P.p, 256, smem, st>>>(P.A, P.p, P.dinv, nullptr, P.Ainv, 0);
+}
+
+void launch_inv_gemv(const ProblemDev& P, const double* b, double* x, int accumulate,
+                     cudaStream_t st) {
+  k_inv_gemv<<<(P.p * 32 + 255) / 256, 256, 0, st>>>(P.p, P.Ainv, b, x, accumulate);
+}
 
 void launch_cheb2mono(const ProblemDev& P, cudaStream_t st) {
   k_cheb2mono<<<(P.pm + 127) / 128, 128, 0, st>>>(P.pm, P.conv_row, P.conv_l, P.conv_c, P.alpha,

@@ -128,6 +128,9 @@ int bsde_set_grid_impl(GridHost& g, int d, int n, const double* lo, const double
 Problem::~Problem() {
   destroy_graph();
   for (auto e : events) cudaEventDestroy(e);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (side) cudaStreamDestroy(side);
 }
 
 void Problem::destroy_graph() {
@@ -180,6 +183,7 @@ size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int t
   add((size_t)n * chunks * 8);
   add((size_t)n * 8);
   add((size_t)p * p * 8);
+  add((size_t)p * p * 8);  // inverse of the Gram matrix
   add((size_t)p * 8 * 4);
   add((size_t)(n > p ? n : p) * 8);
   add((size_t)p * 8);
@@ -348,6 +352,7 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     P.partial = (double*)take((size_t)n * s.chunks * 8);
     P.c = (double*)take((size_t)n * 8);
     P.A = (double*)take((size_t)p * p * 8);
+    P.Ainv = (double*)take((size_t)p * p * 8);
     P.rhs = (double*)take((size_t)p * 8 * 4);
     P.delta = P.rhs + p;
     P.res = P.rhs + 2 * p;
@@ -425,6 +430,19 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
   const uint32_t kp = grid.resample ? (uint32_t)k : 0u;
   launch_points(model, grid, dev, kp, st);
   launch_basis(model, grid, dev, mixed, st);
+  if (!shape.qr) {
+    if (!side) {
+      int lo = 0, hi = 0;
+      cudaDeviceGetStreamPriorityRange(&lo, &hi);
+      if (cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        err = "side stream creation failed";
+        return BSDE_ERR_CUDA;
+      }
+    }
+    cudaEventRecord(ev_fork, st);
+  }
   if (dev.dense) launch_cheb2mono(dev, st);
   if (rec) record(ev[0], st);
   cudaError_t e = launch_paths(model, grid, dev, shape.M, shape.N, (uint32_t)k, mixed, shape.tpb,
@@ -439,27 +457,42 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
   if (shape.qr) {
     // refit by pivoted QR on the design matrix (FP64)
     if (rec) record(ev[3], st);
+    if (rec) record(ev[6], st);
+    if (rec) record(ev[7], st);
     if (rec) record(ev[4], st);
     launch_qr_solve(dev, st);
   } else {
+    // the Gram matrix, its Cholesky factor and its inverse depend only on
+    // the points: they run on the side stream while the paths run, and the
+    // refit after the paths is a product with the inverse plus FP64
+    // refinement steps against the exact normal equations
+    if (cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) {
+      err = "side stream wait failed";
+      return BSDE_ERR_CUDA;
+    }
+    if (rec) record(ev[3], side);
     if (mixed) {
-      e = launch_gram_tc(dev, st);
+      e = launch_gram_tc(dev, side);
       if (e != cudaSuccess) {
         err = std::string("tensor-core Gram launch failed: ") + cudaGetErrorString(e);
         return BSDE_ERR_CUDA;
       }
     } else {
-      launch_gram_f64(dev, st);
+      launch_gram_f64(dev, side);
     }
-    if (rec) record(ev[3], st);
+    if (rec) record(ev[6], side);
+    launch_cholesky(dev, side);
+    launch_inverse(dev, side);
+    if (rec) record(ev[7], side);
+    cudaEventRecord(ev_join, side);
     launch_rhs(dev, st);
+    cudaStreamWaitEvent(st, ev_join, 0);
     if (rec) record(ev[4], st);
-    launch_cholesky(dev, st);
-    launch_chol_solve(dev, dev.rhs, dev.delta, st);
-    const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 0);
+    launch_inv_gemv(dev, dev.rhs, dev.delta, 0, st);
+    const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 1);
     for (int r = 0; r < refine; ++r) {
       launch_refine_residual(dev, st);
-      launch_chol_solve(dev, dev.res, dev.delta, st);
+      launch_inv_gemv(dev, dev.res, dev.delta, 1, st);
     }
   }
   if (rec) record(ev[5], st);
@@ -474,11 +507,11 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
 }
 
 int Problem::enqueue_solve(const bsde_solve_params& prm, cudaStream_t st) {
-  const int nev = prm.timing ? 6 * prm.K_it : 0;
+  const int nev = prm.timing ? 8 * prm.K_it : 0;
   if (nev) ensure_events(nev);
   for (int it = 0; it < prm.K_it; ++it) {
     const int rc = enqueue_iteration(prm, prm.k_start + it, st,
-                                     nev && (int)events.size() >= nev ? &events[6 * it] : nullptr);
+                                     nev && (int)events.size() >= nev ? &events[8 * it] : nullptr);
     if (rc != BSDE_OK) return rc;
   }
   return BSDE_OK;
@@ -612,21 +645,26 @@ int Problem::finish_report(const bsde_solve_params& prm, cudaStream_t st, bsde_r
     r.path_steps_per_s = ms_total > 0 ? r.path_steps / (ms_total * 1e-3) : 0.0;
     r.path_launches = prm.K_it;
     r.rank = rank;
-    const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 0);
     const int panels = (shape.p + 31) / 32;
     const int chol = 1 + 3 * panels - 2;
     const int steps_qr = shape.p < shape.n ? shape.p : shape.n;
-    const int refit = shape.qr ? (2 + 2 * steps_qr) : ((mixed ? 2 : 1) + 1 + chol + 1 + refine * 3);
+    const int refine2 = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 1);
+    const int refit = shape.qr ? (2 + 2 * steps_qr)
+                               : ((mixed ? 2 : 1) + 1 + chol + 1 + 1 + refine2 * 3);
     r.kernel_launches = prm.K_it * (2 + (dev.dense ? 1 : 0) + 1 + 1 + refit + 1 + 3);
     // points, basis, paths, reduce, Gram (+ reduce), rhs, Cholesky, solve,
     // refinement (2 GEMVs + solve each), update, read-out (3)
-    if (prm.timing && (int)events.size() >= 6 * prm.K_it) {
+    if (prm.timing && (int)events.size() >= 8 * prm.K_it) {
+      // paths: ev0..ev1; Gram (side stream): ev3..ev6; factor + inverse
+      // (side stream, overlapped with the paths) ev6..ev7 are counted in the
+      // Gram figure; critical-path refit after the paths: ev4..ev5
       double mp = 0, mg = 0, msv = 0;
       for (int k = 0; k < prm.K_it; ++k) {
+        cudaEvent_t* e = &events[8 * k];
         float a = 0, b = 0, c = 0;
-        if (cudaEventElapsedTime(&a, events[6 * k], events[6 * k + 1]) == cudaSuccess) mp += a;
-        if (cudaEventElapsedTime(&b, events[6 * k + 2], events[6 * k + 3]) == cudaSuccess) mg += b;
-        if (cudaEventElapsedTime(&c, events[6 * k + 4], events[6 * k + 5]) == cudaSuccess) msv += c;
+        if (cudaEventElapsedTime(&a, e[0], e[1]) == cudaSuccess) mp += a;
+        if (cudaEventElapsedTime(&b, e[3], e[7]) == cudaSuccess) mg += b;
+        if (cudaEventElapsedTime(&c, e[4], e[5]) == cudaSuccess) msv += c;
       }
       cudaGetLastError();
       r.ms_paths = mp;

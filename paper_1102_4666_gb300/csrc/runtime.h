@@ -79,6 +79,10 @@ class Problem {
   cudaGraphExec_t gexec = nullptr;
   std::string graph_key;
   std::vector<cudaEvent_t> events;  // 6 per iteration when timing
+  // side stream of the overlapped refit: the Gram matrix, its factor and its
+  // inverse depend only on the points, so they run while the paths run
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int choose_launch(int d, int p, int eta, int N, int M, bool mixed, bool dense, int& tpb,
                     int& ppt);
   void ensure_events(int count);
