@@ -252,8 +252,10 @@ def run_ours(args):
 
     cfg = workloads.config(CONFIG)
     cfg["seed"] = rank_seed(cfg["seed"], rank)  # independent problem per rank
+    from paper_1102_4666_gb300 import autotune
+    shape = autotune.lookup(cfg, "mixed") or autotune.tune(cfg, "mixed", n_points=800)
     stream = torch.cuda.Stream(device=dev)
-    s = G.Solver(cfg, precision="mixed", device=local, stream=stream.cuda_stream)
+    s = G.Solver(cfg, precision="mixed", device=local, stream=stream.cuda_stream, launch_shape=shape)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def step(timing=1):
@@ -335,7 +337,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": cfg["name"], "d": 10, "n": cfg["n"], "M": cfg["M"], "N": cfg["N"],
                    "eta": 3, "p": rep0.p, "K_it": cfg["K_it"], "precision": "mixed",
-                   "l2": "flushed between steps (256 MB write)", "graph": True},
+                   "l2": "flushed between steps (256 MB write)", "graph": True,
+                   "paths_launch_shape": list(shape) if shape else None},
         "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,float,10>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": None,

@@ -291,8 +291,12 @@ def torch_allocator():
 class Solver:
     """One context of the C ABI set up from a workload dictionary."""
 
-    def __init__(self, cfg, precision="mixed", device=0, stream=None, torch_memory=True, mem_budget=0):
+    def __init__(self, cfg, precision="mixed", device=0, stream=None, torch_memory=True, mem_budget=0,
+                 launch_shape=None):
         self.cfg = cfg
+        # (threads per CTA, paths per thread) of the path kernel, e.g. from
+        # autotune.lookup()/tune(); None leaves the library's choice
+        self.launch_shape = launch_shape
         o = bsde_create_opts()
         o.device = device
         o.stream = stream
@@ -322,8 +326,13 @@ class Solver:
         lo, hi = _arr(cfg["lo"]), _arr(cfg["hi"])
         return lib().bsde_set_grid(self.h, cfg["n"], ctypes.cast(lo, _dptr), ctypes.cast(hi, _dptr), resample)
 
+    def _shape(self, kw):
+        if self.launch_shape and "paths_tpb" not in kw and "paths_ppt" not in kw:
+            kw = dict(kw, paths_tpb=self.launch_shape[0], paths_ppt=self.launch_shape[1])
+        return kw
+
     def solve(self, check=True, **kw):
-        p = solve_params(self.cfg, **kw)
+        p = solve_params(self.cfg, **self._shape(kw))
         rep = bsde_report()
         rc = lib().bsde_solve(self.h, ctypes.byref(p), ctypes.byref(rep))
         if check:
@@ -334,7 +343,7 @@ class Solver:
         """One iteration from alpha (None: current); returns t, x, c, alpha_next."""
         import numpy as np
         cfg = self.cfg
-        p = solve_params(cfg, **kw)
+        p = solve_params(cfg, **self._shape(kw))
         n, d = cfg["n"], cfg["d"]
         P = self.basis_size(p.eta, p.q)
         t = np.zeros(n); x = np.zeros(d * n); c = np.zeros(n); an = np.zeros(P)
