@@ -36,6 +36,12 @@ CONFIG = "c4"
 # ~110 per step at N = 100; only the 300 of the Euler step are counted.
 FLOPS_PER_PATH_STEP = 300.0
 SMS, FP32_LANES = 152, 128
+# DRAM bytes (read + write) of one path-kernel launch from the ncu capture in
+# profiles/k_paths_d10_dense_n800.md (n = 800 points: 163.3 KB read, 1.0 KB
+# written), scaled to a launch over n points: the kernel reads the points and
+# coefficients and writes one partial sum per (point, chunk), both
+# proportional to n.
+PATH_TRAFFIC_BYTES_PER_POINT = (163328.0 + 1024.0) / 800.0
 
 
 def env_rank():
@@ -339,9 +345,11 @@ def run_ours(args):
                    "eta": 3, "p": rep0.p, "K_it": cfg["K_it"], "precision": "mixed",
                    "l2": "flushed between steps (256 MB write)", "graph": True,
                    "paths_launch_shape": list(shape) if shape else None},
-        "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,float,10>", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,EV_DENSE3,CC,float,10>",
+                     "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": None,
+                     "traffic": PATH_TRAFFIC_BYTES_PER_POINT * cfg["n"],
+                     "traffic_basis": "dram read+write per launch from the n=800 ncu capture, scaled by n",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock %.0f MHz" % sm_mhz,
                      "flops_per_path_step": FLOPS_PER_PATH_STEP, "path_kernel_ms": path_ms},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -52,7 +52,8 @@ struct Args {
   R rho;  // constant correlation (dense evaluation)
   R kc[D];  // -2 log2(e) kappa_j: e^{2 (x - kappa)} = 2^{x 2 log2(e) + kc}
   uint32_t k;
-  uint32_t key0, key1;  // Philox key as kernel parameters: warp-uniform round keys
+  uint32_t key0, key1;  // Philox key
+  uint32_t rk0[10], rk1[10];  // its ten round keys (kernel-parameter constants)
   const double* pt;
   const double* px;
   const R* alpha;
@@ -72,6 +73,26 @@ __device__ __forceinline__ float uniform_frac<float>(uint32_t w) {
 template <>
 __device__ __forceinline__ double uniform_frac<double>(uint32_t w) {
   return ((double)w + 0.5) * 2.3283064365386962890625e-10;
+}
+
+// Philox4x32-10 with the round keys read from the kernel parameters (the
+// same function as Philox in common.cuh; the xor with the round key then
+// takes its operand from the constant bank instead of a key-schedule add)
+template <typename R, int D>
+__device__ __forceinline__ uint4 philox_rk(const Args<R, D>& a, uint32_t c0, uint32_t c1,
+                                           uint32_t c2, uint32_t c3) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u;
+    const uint64_t p1 = (uint64_t)c2 * 0xCD9E8D57u;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ a.rk0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ a.rk1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
 }
 
 // r = 1 / (e^{2 (x - kappa_j)} + 1), so that tanh(x - kappa_j) = 1 - 2 r
@@ -97,7 +118,15 @@ __device__ __forceinline__ R sigma_j(const Args<R, D>& a, const R* tabs, int j, 
     return a.va[j];
   } else if constexpr (VK == VK_TANH) {
     const R r = tanh_r(a, j, xj);
-    const R A = tabs[2 * j], B = tabs[2 * j + 1];
+    R A, B;
+    if constexpr (sizeof(R) == 4) {
+      const float2 ab = reinterpret_cast<const float2*>(tabs)[j];  // one 64-bit load
+      A = ab.x;
+      B = ab.y;
+    } else {
+      A = tabs[2 * j];
+      B = tabs[2 * j + 1];
+    }
     if (a.absflag) return A + B * Math<R>::fabs(R(1) - R(2) * r);
     return A + B * r;
   } else {
@@ -185,8 +214,9 @@ __device__ __forceinline__ void term(const R* __restrict__ tb, int S, int eta, i
 // repeated variate.  All loop indices are compile-time constants.
 template <typename R, int D>
 __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __restrict__ beta,
-                                            const R* z, const R* zT, const R* bt, const R* st,
-                                            R& u, R& gen, R& uT) {
+                                            const R (&z)[D + 1], const R (&zT)[D + 1],
+                                            const R (&bt)[D + 1], const R (&st)[D + 1], R& u,
+                                            R& gen, R& uT) {
   constexpr int DP = D + 1;
   constexpr int NQ = DP * (DP + 1) / 2;
   const R* bg = beta + 1;
@@ -329,7 +359,6 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
   for (int q = tid; q < DP * DP; q += tpb) s_cp[q] = (&a.Cp[0][0])[q];
   __syncthreads();
 
-  const Philox ph{a.key0, a.key1};
   const uint32_t tagU = (TAG_U << 24) | a.k, tagZ = (TAG_Z << 24) | a.k, tagB = (TAG_B << 24) | a.k;
   constexpr int G = 4 / gcd_c(D, 4);  // steps per group: G*D normals = whole Philox blocks
   constexpr int NB = G * D / 4;
@@ -341,7 +370,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const int m = chunk * ppc + jp * tpb + tid;
     if (m >= a.M) break;
     // the uniform random time: U = (s* + theta) / N from one 32-bit word
-    const uint4 ou = ph(0u, (uint32_t)m, (uint32_t)i, tagU);
+    const uint4 ou = philox_rk(a, 0u, (uint32_t)m, (uint32_t)i, tagU);
     const uint64_t wN = (uint64_t)ou.x * (uint64_t)a.N;
     const int sstar = (int)(wN >> 32);
     const R theta = uniform_frac<R>((uint32_t)wN);
@@ -360,7 +389,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
       const uint32_t blk0 = (uint32_t)(s0 / G) * (uint32_t)NB;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        const uint4 o = ph(blk0 + b, (uint32_t)m, (uint32_t)i, tagZ);
+        const uint4 o = philox_rk(a, blk0 + b, (uint32_t)m, (uint32_t)i, tagZ);
         Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1], sqh);
         Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3], sqh);
       }
@@ -400,7 +429,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     R zb[NBB * 4];
 #pragma unroll
     for (int b = 0; b < NBB; ++b) {
-      const uint4 o = ph((uint32_t)b, (uint32_t)m, (uint32_t)i, tagB);
+      const uint4 o = philox_rk(a, (uint32_t)b, (uint32_t)m, (uint32_t)i, tagB);
       Math<R>::box_muller(o.x, o.y, zb[4 * b + 0], zb[4 * b + 1], R(1));
       Math<R>::box_muller(o.z, o.w, zb[4 * b + 2], zb[4 * b + 3], R(1));
     }
@@ -572,6 +601,10 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.k = k;
   a.key0 = P.seed_key[0];
   a.key1 = P.seed_key[1];
+  for (int r = 0; r < 10; ++r) {
+    a.rk0[r] = a.key0 + (uint32_t)r * 0x9E3779B9u;
+    a.rk1[r] = a.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
   a.pt = P.t;
   a.px = P.x;
   if constexpr (sizeof(R) == 4)
