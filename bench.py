@@ -36,12 +36,12 @@ CONFIG = "c4"
 # ~110 per step at N = 100; only the 300 of the Euler step are counted.
 FLOPS_PER_PATH_STEP = 300.0
 SMS, FP32_LANES = 152, 128
-# DRAM bytes (read + write) of one path-kernel launch from the ncu capture in
-# profiles/k_paths_d10_dense_n800.md (n = 800 points: 163.3 KB read, 1.0 KB
-# written), scaled to a launch over n points: the kernel reads the points and
-# coefficients and writes one partial sum per (point, chunk), both
-# proportional to n.
-PATH_TRAFFIC_BYTES_PER_POINT = (163328.0 + 1024.0) / 800.0
+# DRAM bytes (read + write) of one path-kernel launch per point, from the ncu
+# capture summarised in profiles/k_paths_d10_dense_n800.md, scaled to a
+# launch over n points (the kernel reads the points and coefficients and
+# writes one partial sum per (point, chunk), both proportional to n).  None
+# while the kernel has changed since the capture.
+PATH_TRAFFIC_BYTES_PER_POINT = None
 
 
 def env_rank():
@@ -197,7 +197,7 @@ def run_profile_case(args):
     return 0
 
 
-def run_serving(n_requests, precision="mixed", slots=16, seed=7, load=0.8):
+def run_serving(n_requests, precision="mixed", slots=16, seed=7, load=0.8, policy="fifo"):
     """Continuous-batching serving mix: a seeded Poisson stream of pricing
     requests of uneven d, n, M and degree (workloads.serving_mix) submitted
     at their arrival times to bsde_server; arrival rate calibrated to `load`
@@ -218,7 +218,7 @@ def run_serving(n_requests, precision="mixed", slots=16, seed=7, load=0.8):
     srv.close()
     rate = load * cap / mean_steps
     rng = __import__("random").Random(seed)
-    srv = G.Server(max_slots=slots, precision=precision)
+    srv = G.Server(max_slots=slots, precision=precision, policy=policy)
     t_start = time.perf_counter()
     t_arr = 0.0
     ids = []
@@ -237,7 +237,7 @@ def run_serving(n_requests, precision="mixed", slots=16, seed=7, load=0.8):
         if rep is None or rep.status != 0:
             bad += 1
     srv.close()
-    return {"requests": len(reqs), "precision": precision, "slots": slots,
+    return {"requests": len(reqs), "precision": precision, "slots": slots, "policy": policy,
             "arrival_rate_hz": rate, "calibrated_capacity_path_steps_per_s": cap, "load": load,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "path_steps_per_s": st["path_steps"] / wall, "busy_path_steps_per_s": st["path_steps_per_s"],
@@ -259,7 +259,7 @@ def run_ours(args):
     cfg = workloads.config(CONFIG)
     cfg["seed"] = rank_seed(cfg["seed"], rank)  # independent problem per rank
     from paper_1102_4666_gb300 import autotune
-    shape = autotune.lookup(cfg, "mixed") or autotune.tune(cfg, "mixed", n_points=800)
+    shape = autotune.lookup(cfg, "mixed") or autotune.tune(cfg, "mixed", repeats=3)
     stream = torch.cuda.Stream(device=dev)
     s = G.Solver(cfg, precision="mixed", device=local, stream=stream.cuda_stream, launch_shape=shape)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -329,12 +329,21 @@ def run_ours(args):
     s.close()
     if rank != 0:
         return 0
+    # the same d = 10 American basket put with the penalty weight of the
+    # paper's American experiments (omega = 1), where the iteration converges
+    chk = G.Solver(workloads.config(CONFIG, **{"lambda": 1.0}), precision="mixed", device=local)
+    r1 = chk.solve(use_graph=1)
+    chk.close()
+    omega1 = {"lambda": 1.0, "price": r1.price, "delta": list(r1.delta[:10]),
+              "resid_l2": list(r1.resid_l2[:cfg["K_it"]]), "status": r1.status}
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     launch_steps = cfg["n"] * cfg["M"] * cfg["N"]
     achieved = FLOPS_PER_PATH_STEP * launch_steps / (path_ms * 1e-3) / 1e12 if path_ms > 0 else None
     cpu = cpu_oracle_rate(cfg, budget_s=args.cpu_budget) if not args.no_cpu else None
     serving = run_serving(args.serving_requests) if args.serving_requests > 0 else None
+    serving_sjf = (run_serving(args.serving_requests, slots=4, policy="shortest")
+                   if args.serving_requests > 0 else None)
     rep0 = reps[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -348,7 +357,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,EV_DENSE3,CC,float,10>",
                      "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": PATH_TRAFFIC_BYTES_PER_POINT * cfg["n"],
+                     "traffic": (PATH_TRAFFIC_BYTES_PER_POINT * cfg["n"]
+                                 if PATH_TRAFFIC_BYTES_PER_POINT else None),
                      "traffic_basis": "dram read+write per launch from the n=800 ncu capture, scaled by n",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock %.0f MHz" % sm_mhz,
                      "flops_per_path_step": FLOPS_PER_PATH_STEP, "path_kernel_ms": path_ms},
@@ -358,9 +368,15 @@ def run_ours(args):
                    "reasons": clk.get("reasons")},
         "fp64_plain": fp64,
         "solve": {"price": rep0.price, "delta0": rep0.delta[0], "ms_paths": rep0.ms_paths,
-                  "ms_gram": rep0.ms_gram, "ms_solve": rep0.ms_solve, "ms_total": rep0.ms_total},
+                  "ms_gram": rep0.ms_gram, "ms_solve": rep0.ms_solve, "ms_total": rep0.ms_total,
+                  "resid_l2_first_last": [rep0.resid_l2[0], rep0.resid_l2[cfg["K_it"] - 1]],
+                  "note": "penalty lambda T = 100 is far outside the range where the Picard "
+                          "iteration contracts (error bound (lambda T)^k / k!): the iterates of this "
+                          "throughput workload grow over its 12 iterations; see solve_omega1"},
+        "solve_omega1": omega1,
         "cpu_baseline": cpu,
         "serving": serving,
+        "serving_shortest_first": serving_sjf,
     }
     print(json.dumps(line))
     if world > 1:

@@ -301,11 +301,16 @@ BSDE_API int bsde_corrections_noalloc(const bsde_sigma* sigma, double r, const b
  * ---------------------------------------------------------------------- */
 typedef struct bsde_server bsde_server;
 
+#define BSDE_POLICY_FIFO 0     /* admit in arrival order                        */
+#define BSDE_POLICY_SHORTEST 1 /* admit the queued request with the fewest
+                                  path-steps (K_it n M N) first             */
+
 typedef struct {
   int device;
   int max_slots;        /* requests resident at once (1..64)             */
   size_t mem_budget;    /* device bytes for resident requests            */
   int precision;        /* BSDE_PREC_*                                   */
+  int policy;           /* BSDE_POLICY_*                                 */
 } bsde_server_opts;
 
 typedef struct {

@@ -96,7 +96,7 @@ class bsde_report(ctypes.Structure):
 
 class bsde_server_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_slots", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("policy", ctypes.c_int)]
 
 
 class bsde_request(ctypes.Structure):
@@ -415,9 +415,10 @@ def basis_indices(d, eta, q=1.0):
 class Server:
     """Continuous-batching server of the C ABI (bsde_server_*)."""
 
-    def __init__(self, device=0, max_slots=16, mem_budget=0, precision="mixed"):
+    def __init__(self, device=0, max_slots=16, mem_budget=0, precision="mixed", policy="fifo"):
         o = bsde_server_opts()
         o.device, o.max_slots, o.mem_budget = device, max_slots, mem_budget
+        o.policy = 1 if policy == "shortest" else 0
         o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
         h = ctypes.c_void_p()
         rc = lib().bsde_server_create(ctypes.byref(h), ctypes.byref(o))

@@ -55,24 +55,38 @@ struct Math;
 
 template <>
 struct Math<float> {
-  // Box-Muller pair from two 32-bit words: u = (w + 1/2) 2^-32 in (0,1]
+  // Box-Muller pair from two 32-bit words, u = (w + 1/2) 2^-32 in (0,1],
+  // returning scale * (z0, z1).  k = bm_factor(scale) = -2 ln(2) scale^2
+  // folds the scale and the change of logarithm base into one product:
+  // (scale r)^2 = -2 ln(u0) scale^2 = log2(u0) k.
+  __device__ __forceinline__ static float bm_factor(float scale) {
+    return -1.3862943611198906f * scale * scale;
+  }
   __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, float& z0,
-                                                    float& z1, float scale) {
+                                                    float& z1, float k) {
     const float u0 = fmaf(__uint2float_rn(w0), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float u1 = fmaf(__uint2float_rn(w1), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    float lg;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(u0));
     // sqrt(r2) as r2 * rsqrt(r2) (r2 >= 1e-30 keeps rsqrt finite)
-    const float r2 = fmaxf(-2.0f * __logf(u0), 1e-30f);
-    const float rad = r2 * rsqrtf(r2) * scale;
-    float s, c;
-    // angle 2 pi u1 - pi keeps the argument in (-pi, pi]; cos/sin flip sign
-    __sincosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f), &s, &c);
+    const float r2 = fmaxf(lg * k, 1e-30f);
+    float rs, s, c;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r2));
+    const float rad = r2 * rs;
+    // angle 2 pi u1 - pi in (-pi, pi], straight from w1; cos/sin flip sign.
+    // The .ftz forms: no operand here is subnormal (r2 >= 1e-30, |angle| is
+    // 0 or above 1e-9), so flushing changes no result and saves the
+    // subnormal handling of the non-ftz forms.
+    const float ang = fmaf(__uint2float_rn(w1), 1.4629180792671596e-09f, -3.1415926528f);
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(ang));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(ang));
     z0 = -rad * c;
     z1 = -rad * s;
   }
-  __device__ __forceinline__ static float exp(float x) { return __expf(x); }
-  __device__ __forceinline__ static float tanh(float x) {
-    // 1 - 2 / (e^{2x} + 1): exact limits +-1, absolute error ~1e-7
-    return 1.0f - __fdividef(2.0f, __expf(2.0f * x) + 1.0f);
+  // e^x = 2^(x log2 e); results below the normal range flush to 0
+  __device__ __forceinline__ static float exp(float x) {
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(x * 1.4426950408889634f));
+    return e;
   }
   __device__ __forceinline__ static float sqrt(float x) { return sqrtf(x); }
   __device__ __forceinline__ static float sin(float x) { return sinf(x); }
@@ -83,6 +97,8 @@ struct Math<float> {
 
 template <>
 struct Math<double> {
+  // the FP64 path applies the scale after the square root
+  __device__ __forceinline__ static double bm_factor(double scale) { return scale; }
   __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, double& z0,
                                                     double& z1, double scale) {
     const double u0 = ((double)w0 + 0.5) * 2.3283064365386962890625e-10;
@@ -94,7 +110,6 @@ struct Math<double> {
     z1 = rad * s;
   }
   __device__ __forceinline__ static double exp(double x) { return ::exp(x); }
-  __device__ __forceinline__ static double tanh(double x) { return ::tanh(x); }
   __device__ __forceinline__ static double sqrt(double x) { return ::sqrt(x); }
   __device__ __forceinline__ static double sin(double x) { return ::sin(x); }
   __device__ __forceinline__ static double exp_acc(double x) { return ::exp(x); }

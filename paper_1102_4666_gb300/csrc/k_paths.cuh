@@ -13,9 +13,10 @@
 // every normal is a compile-time offset.  The time factors of the local
 // volatility, the coefficients alpha and the multi-index table are staged
 // in shared memory once per CTA.  The random time tau falls inside step s*;
-// the main loop only records X_{s*} and the step's increment, and X_tau is
-// drawn after the loop through a Brownian bridge (no divergent branch in
-// the loop).  u^k and its derivatives at (tau, X_tau) and u^k(T, X_T) come
+// the main loop only records the states before and after step s* (for the
+// Chebyshev-table kernels behind a warp vote, so that a warp none of whose
+// paths is at its step s* skips the copies), and X_tau is drawn after the
+// loop through a Brownian bridge.  u^k and its derivatives at (tau, X_tau) and u^k(T, X_T) come
 // from per-thread Chebyshev tables in shared memory (layout [slot][thread],
 // conflict-free), or, when the basis has total degree <= 3 (EV = EV_DENSE3),
 // from the monomial coefficients beta of u^k (converted from the Chebyshev
@@ -29,7 +30,9 @@
 
 namespace paths {
 
-enum { VK_CONST = 0, VK_TANH = 1, VK_DUPIRE = 2 };
+// volatility families: constant, a + phi(t) tanh(x - kappa) (sin/tanh),
+// Dupire's, and a + phi(t) |tanh(x - kappa)| (abs/tanh)
+enum { VK_CONST = 0, VK_TANH = 1, VK_DUPIRE = 2, VK_TANH_ABS = 3 };
 enum { EV_TABLES = 0, EV_DENSE3 = 1 };
 
 // monomials of total degree <= 3 in dp variates: C(dp + 3, 3)
@@ -47,7 +50,7 @@ struct Args {
   R Cp[D + 1][D + 1];  // correlation padded with a zero time row/column
   R ctr[D + 1], sc[D + 1];  // xi_v = (y_v - ctr_v) sc_v
   int N, M, n, p, eta, chunks, tpb, ppt, tab_stride;
-  int payoff, obstacle, absflag, vol_sin;
+  int payoff, obstacle, vol_sin;
   R vb;
   R rho;  // constant correlation (dense evaluation)
   R kc[D];  // -2 log2(e) kappa_j: e^{2 (x - kappa)} = 2^{x 2 log2(e) + kc}
@@ -95,29 +98,31 @@ __device__ __forceinline__ uint4 philox_rk(const Args<R, D>& a, uint32_t c0, uin
   return make_uint4(c0, c1, c2, c3);
 }
 
-// r = 1 / (e^{2 (x - kappa_j)} + 1), so that tanh(x - kappa_j) = 1 - 2 r
-template <typename R, int D>
+// r = 1 / (e^{2 y} + 1), so that tanh(y) = 1 - 2 r, with y = x - kappa_j
+// (ABS: y = |x - kappa_j|, since |tanh(x - kappa)| = tanh(|x - kappa|))
+template <bool ABS, typename R, int D>
 __device__ __forceinline__ R tanh_r(const Args<R, D>& a, int j, R xj) {
   if constexpr (sizeof(R) == 4) {
     float e, r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(fmaf(xj, 2.8853900817779268f, a.kc[j])));
+    const float t = fmaf(xj, 2.8853900817779268f, a.kc[j]);  // 2 log2(e) (x - kappa)
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(ABS ? fabsf(t) : t));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.0f));
     return r;
   } else {
-    return 1.0 / (::exp(2.0 * (xj - a.kappa[j])) + 1.0);
+    const double y = xj - a.kappa[j];
+    return 1.0 / (::exp(2.0 * (ABS ? ::fabs(y) : y)) + 1.0);
   }
 }
 
 // local volatility of asset j at the step whose table row is tabs.  The
-// tanh families keep (A, B) per step and asset: sigma = A + B r for
-// a + phi tanh (A = a + phi, B = -2 phi) and sigma = A + B |1 - 2 r| for
-// a + phi |tanh| (A = a, B = phi), with phi the time factor.
+// tanh families keep (A, B) = (a + phi, -2 phi) per step and asset, with phi
+// the time factor, and sigma = A + B r: a + phi tanh(y) = a + phi (1 - 2 r).
 template <int VK, typename R, int D>
 __device__ __forceinline__ R sigma_j(const Args<R, D>& a, const R* tabs, int j, R xj) {
   if constexpr (VK == VK_CONST) {
     return a.va[j];
-  } else if constexpr (VK == VK_TANH) {
-    const R r = tanh_r(a, j, xj);
+  } else if constexpr (VK == VK_TANH || VK == VK_TANH_ABS) {
+    const R r = tanh_r<VK == VK_TANH_ABS>(a, j, xj);
     R A, B;
     if constexpr (sizeof(R) == 4) {
       const float2 ab = reinterpret_cast<const float2*>(tabs)[j];  // one 64-bit load
@@ -127,7 +132,6 @@ __device__ __forceinline__ R sigma_j(const Args<R, D>& a, const R* tabs, int j, 
       A = tabs[2 * j];
       B = tabs[2 * j + 1];
     }
-    if (a.absflag) return A + B * Math<R>::fabs(R(1) - R(2) * r);
     return A + B * r;
   } else {
     const R dev = Math<R>::exp(xj) * tabs[2] - a.s_dupire;
@@ -222,37 +226,17 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
   const R* bg = beta + 1;
   const R* bq = bg + DP;
   const R* bc3 = bq + NQ;
-  // value at (T, X_T)
-  {
-    R s = beta[0];
-    int iq = 0, it = 0;
-#pragma unroll
-    for (int i = 0; i < DP; ++i) {
-      R bi = bg[i];
-#pragma unroll
-      for (int j = i; j < DP; ++j) {
-        R aij = bq[iq++];
-#pragma unroll
-        for (int k = j; k < DP; ++k) aij += bc3[it++] * zT[k];
-        bi += zT[j] * aij;
-        // keep the coefficient loads of one (i, j) group together: without
-        // this fence the scheduler hoists all of them and runs out of registers
-        asm volatile("" ::: "memory");
-      }
-      s += zT[i] * bi;
-    }
-    uT = s;
-  }
-  // value, d_bt, d_st, d2_st and the weighted Hessian diagonal at (tau, X_tau)
-  R uv = beta[0], ub = R(0), us = R(0), uss = R(0), diag = R(0);
+  // one pass over the coefficients for both points: value, d_bt, d_st,
+  // d2_st and the weighted Hessian diagonal at (tau, X_tau), value at (T, X_T)
+  R uv = beta[0], ub = R(0), us = R(0), uss = R(0), diag = R(0), sT = beta[0];
   int iq = 0, it = 0;
 #pragma unroll
   for (int i = 0; i < DP; ++i) {
-    R bv = bg[i], bb = R(0), bs = R(0), bss = R(0);
+    R bv = bg[i], bb = R(0), bs = R(0), bss = R(0), bT = bg[i];
 #pragma unroll
     for (int j = i; j < DP; ++j) {
       const R q = bq[iq++];
-      R av = q, ab = R(0), as = R(0);
+      R av = q, ab = R(0), as = R(0), aT = q;
       if (i == j && i > 0) diag += R(2) * st[i] * st[i] * q;
 #pragma unroll
       for (int k = j; k < DP; ++k) {
@@ -260,6 +244,7 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
         av += t * z[k];
         ab += t * bt[k];
         if (k > 0) as += t * st[k];
+        aT += t * zT[k];
         if (i == j && j < k && i > 0) diag += R(2) * st[i] * st[i] * t * z[k];
         if (i < j && j == k && j > 0) diag += R(2) * st[j] * st[j] * t * z[i];
         if (i == j && j == k && i > 0) diag += R(6) * st[i] * st[i] * t * z[i];
@@ -273,6 +258,9 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
       } else {
         bs += z[j] * as;
       }
+      bT += zT[j] * aT;
+      // keep the coefficient loads of one (i, j) group together: without
+      // this fence the scheduler hoists all of them and runs out of registers
       asm volatile("" ::: "memory");
     }
     // (z_i, bt_i, st_i, 0) * (bv, bb, bs, bss)
@@ -285,7 +273,9 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
       us += z[i] * bs;
       uss += z[i] * bss;
     }
+    sT += zT[i] * bT;
   }
+  uT = sT;
   (void)us;
   u = uv;
   gen = ub + R(0.5) * ((R(1) - a.rho) * diag + a.rho * uss);
@@ -328,6 +318,8 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
   for (int j = 0; j < D; ++j) x0[j] = (R)a.px[(size_t)j * a.n + i];
   const R h = (a.T - ti) / (R)a.N;
   const R sqh = Math<R>::sqrt(h);
+  const R bmk = Math<R>::bm_factor(sqh);  // Box-Muller radius factor of the step normals
+  const R bm1 = Math<R>::bm_factor(R(1));
 
   // per-step coefficients of the local volatility (in the precision of the
   // path: accurate sinf/expf for FP32, sin/exp for FP64)
@@ -335,13 +327,10 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const int s = idx / a.tab_stride, c = idx - s * a.tab_stride;
     const R ts = ti + (R)s * h;
     R v = 0;
-    if constexpr (VK == VK_TANH) {
+    if constexpr (VK == VK_TANH || VK == VK_TANH_ABS) {
       const int j = c >> 1;
       const R phi = a.vol_sin ? a.vb * Math<R>::sin((R)(j + 1) + ts) : a.vb * Math<R>::exp_acc(-ts);
-      if (a.absflag)
-        v = (c & 1) ? phi : a.va[j < D ? j : 0];
-      else
-        v = (c & 1) ? R(-2) * phi : a.va[j < D ? j : 0] + phi;
+      v = (c & 1) ? R(-2) * phi : a.va[j < D ? j : 0] + phi;
     } else if constexpr (VK == VK_DUPIRE) {
       const R ew = Math<R>::exp_acc(R(-0.05) * Math<R>::sqrt(ts));
       v = (c == 0) ? R(0.72) * ew
@@ -390,8 +379,8 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         const uint4 o = philox_rk(a, blk0 + b, (uint32_t)m, (uint32_t)i, tagZ);
-        Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1], sqh);
-        Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3], sqh);
+        Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1], bmk);
+        Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3], bmk);
       }
 #pragma unroll
       for (int gs = 0; gs < G; ++gs) {
@@ -399,6 +388,18 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
         if (s < a.N) {
           const R* tabs = tab + s * a.tab_stride;
           const bool hit = (s == sstar);
+          // the vote is over the lanes that reach this step together; a lane
+          // with hit set always votes for itself, so its copies are never
+          // skipped.  Without the vote the copies are 2 D predicated moves per
+          // step; the vote and its branch pay off from d = 3 on, except next
+          // to the dense evaluation, whose registers leave no room for it.
+          constexpr bool VOTE = (EV == EV_TABLES) && D >= 3;
+          const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
+          if (any_hit) {
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+              if (hit) Xs[j] = X[j];
+          }
           R pre = 0;  // running sum of the constant-correlation factor
 #pragma unroll
           for (int j = 0; j < D; ++j) {
@@ -414,12 +415,12 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
             }
             const R sig = sigma_j<VK>(a, tabs, j, X[j]);
             // X + (r - delta_j - sigma^2/2) h + sigma y = X + h rd_j + sigma (y - h sigma / 2)
-            const R xn = sig * (nhh * sig + y) + (h * a.rd[j] + X[j]);
-            if (hit) {
-              Xs[j] = X[j];
-              Xn[j] = xn;
-            }
-            X[j] = xn;
+            X[j] = sig * (nhh * sig + y) + (h * a.rd[j] + X[j]);
+          }
+          if (any_hit) {
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+              if (hit) Xn[j] = X[j];
           }
         }
       }
@@ -430,8 +431,8 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
 #pragma unroll
     for (int b = 0; b < NBB; ++b) {
       const uint4 o = philox_rk(a, (uint32_t)b, (uint32_t)m, (uint32_t)i, tagB);
-      Math<R>::box_muller(o.x, o.y, zb[4 * b + 0], zb[4 * b + 1], R(1));
-      Math<R>::box_muller(o.z, o.w, zb[4 * b + 2], zb[4 * b + 3], R(1));
+      Math<R>::box_muller(o.x, o.y, zb[4 * b + 0], zb[4 * b + 1], bm1);
+      Math<R>::box_muller(o.z, o.w, zb[4 * b + 2], zb[4 * b + 3], bm1);
     }
     const R* tab_s = tab + sstar * a.tab_stride;
     const R bb = Math<R>::sqrt(theta * (R(1) - theta) * h);
@@ -552,6 +553,17 @@ cudaError_t launch_one(const Args<R, D>& a, unsigned grid, int tpb, size_t smem,
   return cudaGetLastError();
 }
 
+template <int EV, bool CC, typename R, int D>
+cudaError_t launch_ev(int vk, const Args<R, D>& a, unsigned grid, int tpb, size_t smem,
+                      cudaStream_t st) {
+  switch (vk) {
+    case VK_CONST: return launch_one<VK_CONST, EV, CC>(a, grid, tpb, smem, st);
+    case VK_TANH: return launch_one<VK_TANH, EV, CC>(a, grid, tpb, smem, st);
+    case VK_TANH_ABS: return launch_one<VK_TANH_ABS, EV, CC>(a, grid, tpb, smem, st);
+    default: return launch_one<VK_DUPIRE, EV, CC>(a, grid, tpb, smem, st);
+  }
+}
+
 template <typename R, int D>
 cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, int M, int N,
                    uint32_t k, int tpb, int ppt, cudaStream_t st) {
@@ -596,7 +608,6 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.tab_stride = (m.vol_kind == 1 || m.vol_kind == 2) ? 2 * D : (D < 3 ? 3 : D);
   a.payoff = m.payoff;
   a.obstacle = m.obstacle;
-  a.absflag = (m.vol_kind == 1) ? 1 : 0;
   a.vol_sin = (m.vol_kind == 2) ? 1 : 0;
   a.k = k;
   a.key0 = P.seed_key[0];
@@ -623,29 +634,22 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
       a.alpha = reinterpret_cast<const R*>(P.beta);
   }
   const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense, a.tab_stride);
-  const int vk = (m.vol_kind == 0) ? VK_CONST : (m.vol_kind == 3) ? VK_DUPIRE : VK_TANH;
+  const int vk = (m.vol_kind == 0)   ? VK_CONST
+                 : (m.vol_kind == 1) ? VK_TANH_ABS
+                 : (m.vol_kind == 3) ? VK_DUPIRE
+                                     : VK_TANH;
   const unsigned grid = (unsigned)P.n * (unsigned)P.chunks;
-  if (dense) {  // the dense evaluation implies a constant correlation
-    if (vk == VK_CONST) return launch_one<VK_CONST, EV_DENSE3, true>(a, grid, tpb, smem, st);
-    if (vk == VK_TANH) return launch_one<VK_TANH, EV_DENSE3, true>(a, grid, tpb, smem, st);
-    return launch_one<VK_DUPIRE, EV_DENSE3, true>(a, grid, tpb, smem, st);
-  }
-  if (cc) {
-    if (vk == VK_CONST) return launch_one<VK_CONST, EV_TABLES, true>(a, grid, tpb, smem, st);
-    if (vk == VK_TANH) return launch_one<VK_TANH, EV_TABLES, true>(a, grid, tpb, smem, st);
-    return launch_one<VK_DUPIRE, EV_TABLES, true>(a, grid, tpb, smem, st);
-  }
-  if (vk == VK_CONST) return launch_one<VK_CONST, EV_TABLES, false>(a, grid, tpb, smem, st);
-  if (vk == VK_TANH) return launch_one<VK_TANH, EV_TABLES, false>(a, grid, tpb, smem, st);
-  return launch_one<VK_DUPIRE, EV_TABLES, false>(a, grid, tpb, smem, st);
+  if (dense) return launch_ev<EV_DENSE3, true>(vk, a, grid, tpb, smem, st);  // implies constant correlation
+  if (cc) return launch_ev<EV_TABLES, true>(vk, a, grid, tpb, smem, st);
+  return launch_ev<EV_TABLES, false>(vk, a, grid, tpb, smem, st);
 }
 
 }  // namespace paths
 
-#define BSDE_PATHS_INSTANTIATE(DV)                                                           \
-  cudaError_t launch_paths_d##DV(const ModelHost& m, const GridHost& g, const ProblemDev& P, \
-                                 int M, int N, uint32_t k, bool mixed, int tpb, int ppt,     \
-                                 cudaStream_t st) {                                          \
-    return mixed ? paths::launch<float, DV>(m, g, P, M, N, k, tpb, ppt, st)                  \
-                 : paths::launch<double, DV>(m, g, P, M, N, k, tpb, ppt, st);                \
+// one translation unit per (d, precision), so that the build compiles them in parallel
+#define BSDE_PATHS_INSTANTIATE(DV, R, SUF)                                                    \
+  cudaError_t launch_paths_d##DV##_##SUF(const ModelHost& m, const GridHost& g,               \
+                                         const ProblemDev& P, int M, int N, uint32_t k,       \
+                                         int tpb, int ppt, cudaStream_t st) {                 \
+    return paths::launch<R, DV>(m, g, P, M, N, k, tpb, ppt, st);                              \
   }

@@ -3,9 +3,11 @@
 // parameter of the kernel).
 #include "k_paths.cuh"
 
-#define DECL(DV)                                                                            \
-  cudaError_t launch_paths_d##DV(const ModelHost&, const GridHost&, const ProblemDev&, int, \
-                                 int, uint32_t, bool, int, int, cudaStream_t);
+#define DECL(DV)                                                                              \
+  cudaError_t launch_paths_d##DV##_f32(const ModelHost&, const GridHost&, const ProblemDev&, int, \
+                                       int, uint32_t, int, int, cudaStream_t);                \
+  cudaError_t launch_paths_d##DV##_f64(const ModelHost&, const GridHost&, const ProblemDev&, int, \
+                                       int, uint32_t, int, int, cudaStream_t);
 DECL(1) DECL(2) DECL(3) DECL(4) DECL(5) DECL(6) DECL(7) DECL(8) DECL(9) DECL(10)
 #undef DECL
 
@@ -19,17 +21,13 @@ size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed, bool 
 
 cudaError_t launch_paths(const ModelHost& m, const GridHost& g, const ProblemDev& P, int M, int N,
                          uint32_t k, bool mixed, int tpb, int ppt, cudaStream_t st) {
+#define CASE(DV)                                                                          \
+  case DV:                                                                                \
+    return mixed ? launch_paths_d##DV##_f32(m, g, P, M, N, k, tpb, ppt, st)               \
+                 : launch_paths_d##DV##_f64(m, g, P, M, N, k, tpb, ppt, st);
   switch (m.d) {
-    case 1: return launch_paths_d1(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 2: return launch_paths_d2(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 3: return launch_paths_d3(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 4: return launch_paths_d4(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 5: return launch_paths_d5(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 6: return launch_paths_d6(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 7: return launch_paths_d7(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 8: return launch_paths_d8(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 9: return launch_paths_d9(m, g, P, M, N, k, mixed, tpb, ppt, st);
-    case 10: return launch_paths_d10(m, g, P, M, N, k, mixed, tpb, ppt, st);
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
     default: return cudaErrorInvalidValue;
   }
+#undef CASE
 }

@@ -38,6 +38,7 @@ struct Req {
   bsde_solve_params prm;
   double t_submit = 0.0, t_done = 0.0;
   size_t bytes = 0;
+  double work = 0.0;  // K_it n M N, the shortest-first key
   std::unique_ptr<Problem> prob;
   cudaStream_t stream = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -60,7 +61,7 @@ struct bsde_server {
   std::map<uint64_t, std::unique_ptr<Req>> done;
   std::vector<cudaStream_t> free_streams;
   size_t used_bytes = 0;
-  int admitting = 0;  // popped from the queue, not yet in running/done
+  std::vector<uint64_t> admitting;  // ids popped from the queue, not yet in running/done
   std::vector<double> latencies_ms;
   double path_steps = 0.0, busy_s = 0.0, busy_since = -1.0;
   uint64_t completed = 0;
@@ -72,10 +73,15 @@ struct bsde_server {
 
 bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
   if (queue.empty() || (int)running.size() >= opts.max_slots) return false;
-  Req* r = queue.front().get();
+  // next request: the oldest (FIFO) or the one with the least work
+  size_t pick = 0;
+  if (opts.policy == BSDE_POLICY_SHORTEST)
+    for (size_t q = 1; q < queue.size(); ++q)
+      if (queue[q]->work < queue[pick]->work) pick = q;
+  Req* r = queue[pick].get();
   if (opts.mem_budget && used_bytes + r->bytes > opts.mem_budget && !running.empty()) return false;
-  std::unique_ptr<Req> req = std::move(queue.front());
-  queue.pop_front();
+  std::unique_ptr<Req> req = std::move(queue[pick]);
+  queue.erase(queue.begin() + pick);
   used_bytes += req->bytes;
   if (busy_since < 0) busy_since = now_s();
   cudaStream_t st;
@@ -86,7 +92,7 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   }
   req->stream = st;
-  ++admitting;
+  admitting.push_back(req->id);
   lk.unlock();
   // device work outside the lock: allocation, capture, graph launch
   req->prob.reset(new Problem());
@@ -99,7 +105,7 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
   cudaEventCreate(&req->e1);
   req->rc = P.start(req->prm, al, 0, st, req->e0, req->e1);
   lk.lock();
-  --admitting;
+  admitting.erase(std::find(admitting.begin(), admitting.end(), req->id));
   if (req->rc != BSDE_OK) {
     // failed before reaching the device: complete immediately
     memset(&req->rep, 0, sizeof(req->rep));
@@ -156,7 +162,7 @@ void bsde_server::loop() {
       busy_since = -1.0;
     }
     if (!progressed) {
-      if (running.empty() && queue.empty() && admitting == 0)
+      if (running.empty() && queue.empty() && admitting.empty())
         cv.wait(lk);
       else
         cv.wait_for(lk, std::chrono::microseconds(200));
@@ -168,7 +174,8 @@ extern "C" {
 
 int bsde_server_create(bsde_server** out, const bsde_server_opts* o) {
   if (!out || !o || o->max_slots < 1 || o->max_slots > 64 ||
-      (o->precision != BSDE_PREC_FP64 && o->precision != BSDE_PREC_MIXED))
+      (o->precision != BSDE_PREC_FP64 && o->precision != BSDE_PREC_MIXED) ||
+      (o->policy != BSDE_POLICY_FIFO && o->policy != BSDE_POLICY_SHORTEST))
     return BSDE_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o->device < 0 || o->device >= ndev) {
@@ -206,6 +213,7 @@ int bsde_server_submit(bsde_server* s, const bsde_request* rq, uint64_t* id) {
     const int tpb = s->opts.precision == BSDE_PREC_MIXED ? 128 : 64;
     r->bytes = Problem::estimate_bytes(r->model.d, rq->n, p, r->prm.M, r->prm.N_steps,
                                        s->opts.precision == BSDE_PREC_MIXED, tpb, 4);
+    r->work = (double)r->prm.K_it * rq->n * (double)r->prm.M * r->prm.N_steps;
     r->t_submit = now_s();
     std::lock_guard<std::mutex> g(s->mu);
     if (s->opts.mem_budget && r->bytes > s->opts.mem_budget) {
@@ -231,6 +239,7 @@ int bsde_server_poll(bsde_server* s, uint64_t id, bsde_report* rep) {
       if (r->id == id) return 0;
     for (auto& r : s->running)
       if (r->id == id) return 0;
+    if (std::find(s->admitting.begin(), s->admitting.end(), id) != s->admitting.end()) return 0;
     s->err = "poll: unknown request id";
     return BSDE_ERR_INVALID_ARG;
   }
@@ -242,7 +251,7 @@ int bsde_server_poll(bsde_server* s, uint64_t id, bsde_report* rep) {
 int bsde_server_drain(bsde_server* s, double timeout_ms) {
   if (!s) return BSDE_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
-  auto pred = [s] { return s->queue.empty() && s->running.empty() && s->admitting == 0; };
+  auto pred = [s] { return s->queue.empty() && s->running.empty() && s->admitting.empty(); };
   if (timeout_ms > 0) {
     if (!s->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred))
       return BSDE_ERR_TIMEOUT;
@@ -258,7 +267,7 @@ int bsde_server_stats_get(bsde_server* s, bsde_server_stats* st) {
   memset(st, 0, sizeof(*st));
   st->completed = s->completed;
   st->queued = s->queue.size();
-  st->running = s->running.size();
+  st->running = s->running.size() + s->admitting.size();
   std::vector<double> l = s->latencies_ms;
   std::sort(l.begin(), l.end());
   auto pct = [&](double q) {

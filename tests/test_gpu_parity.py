@@ -215,7 +215,10 @@ def test_full_size_c4_sampled_points(G, ev):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("kind", ["const", "abs_tanh", "sin_tanh", "dupire"])
-def test_vol_families_fp64(G, kind):
+@pytest.mark.parametrize("prec,ev", [("fp64", 0), ("fp64", 1), ("mixed", 0), ("mixed", 1)])
+def test_vol_families(G, kind, prec, ev):
+    """Every volatility family, in both precisions and both evaluation forms
+    of u^k (dense monomial, per-thread Chebyshev tables)."""
     cfg = workloads.config("c3", n=80, M=96, N=9, eta=2)
     if kind == "const":
         cfg["vol"] = {"kind": "const", "a": [0.15, 0.2, 0.25, 0.3, 0.35]}
@@ -226,11 +229,12 @@ def test_vol_families_fp64(G, kind):
     cfg["div"] = [0.0, 0.01, 0.02, 0.03, 0.1]
     nu = O.multi_index_set(6, 2)
     a0 = _alpha(cfg, nu)
-    s = solver(G, cfg, "fp64")
-    t, x, c, a1 = s.iterate(0, a0)
+    s = solver(G, cfg, prec)
+    t, x, c, a1 = s.iterate(0, a0, eval_mode=ev)
     s.close()
     it = O.iteration(cfg, nu, a0, 0, nthreads=NTH)
-    assert np.max(np.abs(c - it["c"])) < 1e-9 * _scale(cfg, nu, a0, t, x)
+    tol = 1e-9 if prec == "fp64" else MIXED_C_TOL
+    assert np.max(np.abs(c - it["c"])) < tol * _scale(cfg, nu, a0, t, x)
 
 
 def test_eval_price_delta_matches_oracle(G):

@@ -61,3 +61,39 @@ def test_admission_by_memory_budget():
     with pytest.raises(G.BsdeError):
         srv.submit(big)
     srv.close()
+
+
+def _completion_order(policy):
+    """Submit two long requests and then a short one to a one-slot server and
+    return the order in which they complete (0, 1: long; 2: short)."""
+    import time
+
+    import paper_1102_4666_gb300 as G
+    long_req = workloads.config("c3", K_it=2)  # 1e9 path-steps
+    short_req = workloads.config("c3", n=500, M=1000, K_it=1)
+    srv = G.Server(max_slots=1, precision="mixed", policy=policy)
+    ids = [srv.submit(long_req), srv.submit(long_req, seed=99), srv.submit(short_req)]
+    done = []
+    t0 = time.monotonic()
+    while len(done) < 3 and time.monotonic() - t0 < 120.0:
+        for k in (2, 1, 0):  # the short request is looked at first in every sweep
+            if k not in done:
+                rep = srv.poll(ids[k])
+                if rep is not None:
+                    assert rep.status == G.OK
+                    done.append(k)
+        time.sleep(0.0005)
+    srv.close()
+    return done
+
+
+def test_fifo_policy_admits_in_arrival_order():
+    assert _completion_order("fifo") == [0, 1, 2]
+
+
+def test_shortest_first_policy_overtakes_queued_long_requests():
+    """The short request, queued behind a long one, is admitted as soon as
+    the slot frees up, before the second long request."""
+    order = _completion_order("shortest")
+    assert sorted(order) == [0, 1, 2]
+    assert order.index(2) < order.index(1)
