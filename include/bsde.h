@@ -195,9 +195,10 @@ typedef struct {
   double resid_linf[BSDE_MAX_IT];  /* ||alpha^{k+1} - alpha^k||_inf         */
   double ms_total;             /* device time of the whole solve (events)   */
   double ms_paths;             /* device time of the path kernels (timing=1) */
-  double ms_gram;              /* device time of the Gram matrix, its Cholesky
-                                  factor and inverse (timing=1; on a side
-                                  stream, overlapped with the path kernel)   */
+  double ms_gram;              /* device time of the Gram matrices, their
+                                  Cholesky factors and inverses, built for a
+                                  group of iterations ahead of their path
+                                  kernels (timing=1)                         */
   double ms_solve;             /* device time of the refit after the paths
                                   (RHS, inverse products, refinement; the
                                   whole pivoted-QR refit with ls_mode 1)     */

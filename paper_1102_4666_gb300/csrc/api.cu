@@ -174,7 +174,7 @@ int bsde_iterate(bsde_ctx* c, const bsde_solve_params* prm, int k, const double*
       cudaMemsetAsync(P.dev.alpha, 0, (size_t)p * 8, c->stream);
       cudaMemsetAsync(P.dev.alpha32, 0, (size_t)p * 4, c->stream);
     }
-    rc = P.enqueue_iteration(p1, k, c->stream, nullptr);
+    rc = P.enqueue_block(p1, k, 1, c->stream, nullptr);
     if (rc != BSDE_OK) return fail(c, rc, P.err);
     cudaError_t e = cudaSuccess;
     if (t_out) e = cudaMemcpyAsync(t_out, P.dev.t, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream);

@@ -149,14 +149,15 @@ struct ProblemDev {
   float* Blo = nullptr;       // [p_pad][n_pad] tf32-rounded remainder (mixed)
   double* partial = nullptr;  // [n][chunks] per-chunk sums of a_m
   double* c = nullptr;        // [n] corrections
-  double* A = nullptr;        // [p][p] Gram matrix, then its Cholesky factor
+  double* A = nullptr;        // [nfact][p][p] Gram matrices, then their Cholesky factors
   float* gram_part = nullptr; // split-K partial tiles of the tensor-core Gram
   double* rhs = nullptr;      // [p]
   double* delta = nullptr;    // [p] solution of the normal equations
   double* res = nullptr;      // [p] refinement residual
-  double* v = nullptr;        // [max(n, p)] B delta; original diagonal during Cholesky
-  double* dinv = nullptr;     // [p] reciprocal diagonal of the Cholesky factor
-  double* Ainv = nullptr;     // [p][p] inverse of the Gram matrix (overlapped refit)
+  double* v = nullptr;        // [max(n, p)] B delta
+  double* dinv = nullptr;     // [nfact][p] reciprocal diagonals of the Cholesky factors
+  double* diag0 = nullptr;    // [nfact][p] original diagonals (relative pivot test)
+  double* Ainv = nullptr;     // [nfact][p][p] inverses of the Gram matrices
   double* alpha = nullptr;    // [p] coefficients (FP64 master)
   float* alpha32 = nullptr;   // [p] FP32 copy for the mixed path kernel
   uint2* pairs = nullptr;     // [p] packed (variate, degree) bytes
@@ -208,8 +209,8 @@ void launch_gram_f64(const ProblemDev& P, cudaStream_t st);
 cudaError_t launch_gram_tc(const ProblemDev& P, cudaStream_t st);
 int gram_tc_splits(const ProblemDev& P);
 void launch_rhs(const ProblemDev& P, cudaStream_t st);
-void launch_cholesky(const ProblemDev& P, cudaStream_t st);
-void launch_chol_solve(const ProblemDev& P, const double* b, double* x, cudaStream_t st);
+// batched over nb Gram matrices (P.A, P.dinv, P.diag0, P.Ainv hold nb of them)
+void launch_cholesky(const ProblemDev& P, int nb, cudaStream_t st);
 void launch_refine_residual(const ProblemDev& P, cudaStream_t st);
 void launch_update(const ProblemDev& P, int k, cudaStream_t st);
 void launch_eval_x0(const ModelHost& m, const GridHost& g, const ProblemDev& P, int k,
@@ -220,6 +221,6 @@ void launch_eval_points(const ModelHost& m, const GridHost& g, const ProblemDev&
 size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed, bool dense);
 void launch_cheb2mono(const ProblemDev& P, cudaStream_t st);
 void launch_qr_solve(const ProblemDev& P, cudaStream_t st);
-void launch_inverse(const ProblemDev& P, cudaStream_t st);
+void launch_inverse(const ProblemDev& P, int nb, cudaStream_t st);
 void launch_inv_gemv(const ProblemDev& P, const double* b, double* x, int accumulate, cudaStream_t st);
 int paths_supported_d(int d);

@@ -90,10 +90,16 @@ __global__ void __launch_bounds__(256) k_gram_f64(int n, int n_pad, int p,
   }
 }
 
+// The factorisation kernels work on a batch of Gram matrices, one per
+// blockIdx.y: matrix z is A + z p^2, with its original diagonal at
+// diag0 + z p, its reciprocal factor diagonal at dinv + z p and its inverse
+// at Ainv + z p^2.
+
 // original diagonal of A, for the relative pivot test of the factorisation
 __global__ void k_save_diag(const double* __restrict__ A, int p, double* __restrict__ diag0) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < p) diag0[j] = A[(size_t)j * p + j];
+  const size_t z = blockIdx.y;
+  if (j < p) diag0[z * p + j] = A[z * p * p + (size_t)j * p + j];
 }
 
 // Right-looking blocked Cholesky, panel width 32, lower factor in place.
@@ -106,6 +112,10 @@ __global__ void __launch_bounds__(32) k_chol_diag(double* __restrict__ A, int p,
                                                   const double* __restrict__ diag0,
                                                   double* __restrict__ dinv) {
   __shared__ double Dg[32][33];
+  const size_t z = blockIdx.y;
+  A += z * p * p;
+  diag0 += z * p;
+  dinv += z * p;
   const int nb = min(32, p - j0);
   const int lane = threadIdx.x;
   for (int q = lane; q < 32 * 32; q += 32) {
@@ -151,6 +161,9 @@ __global__ void __launch_bounds__(32) k_chol_trsm(double* __restrict__ A, int p,
                                                   const double* __restrict__ dinv) {
   __shared__ double Dg[32][33];
   __shared__ double di[32];
+  const size_t z = blockIdx.y;
+  A += z * p * p;
+  dinv += z * p;
   const int nb = min(32, p - j0);
   for (int q = threadIdx.x; q < 32 * 32; q += 32) {
     const int r = q >> 5, c = q & 31;
@@ -180,6 +193,7 @@ __global__ void __launch_bounds__(32) k_chol_trsm(double* __restrict__ A, int p,
 // trailing update A22 -= L21 L21^T on the lower triangle, 32x32 tiles
 __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ A, int p, int j0) {
   __shared__ double Lr[32][33], Lc[32][33];
+  A += (size_t)blockIdx.y * p * p;
   const int nb = min(32, p - j0);
   const int base = j0 + nb;
   const int m = p - base;
@@ -217,15 +231,18 @@ __global__ void __launch_bounds__(256) k_chol_update(double* __restrict__ A, int
 // Warp 0 solves each 32x32 diagonal block with shuffles; all threads then
 // update the rest of the vector with that block's 32 columns (forward: a
 // row segment per thread; backward: coalesced column reads).  One CTA.
-// With b == nullptr, CTA j solves A x = e_j and writes column j of A^{-1}
-// to x + j p (the inverse used by the overlapped refit).
+// With b == nullptr, CTA (j, z) solves A_z x = e_j and writes column j of
+// A_z^{-1} to x + z p^2 + j p (the inverses used by the refit).
 __global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ A, int p,
                                                     const double* __restrict__ dinv,
                                                     const double* __restrict__ b,
                                                     double* __restrict__ x, int accumulate) {
   extern __shared__ double yv[];  // p
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (b == nullptr) x += (size_t)blockIdx.x * p;
+  const size_t z = blockIdx.y;
+  A += z * p * p;
+  dinv += z * p;
+  if (b == nullptr) x += z * p * p + (size_t)blockIdx.x * p;
   for (int r = tid; r < p; r += blockDim.x) yv[r] = b ? b[r] : (r == (int)blockIdx.x ? 1.0 : 0.0);
   __syncthreads();
   const int nblk = (p + 31) / 32;
@@ -410,11 +427,11 @@ __global__ void k_inv_gemv(int p, const double* __restrict__ Ainv, const double*
 
 }  // namespace
 
-void launch_inverse(const ProblemDev& P, cudaStream_t st) {
+void launch_inverse(const ProblemDev& P, int nb, cudaStream_t st) {
   const size_t smem = (size_t)P.p * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_chol_solve<<<P.p, 256, smem, st>>>(P.A, P.p, P.dinv, nullptr, P.Ainv, 0);
+  k_chol_solve<<<dim3(P.p, nb), 256, smem, st>>>(P.A, P.p, P.dinv, nullptr, P.Ainv, 0);
 }
 
 void launch_inv_gemv(const ProblemDev& P, const double* b, double* x, int accumulate,
@@ -440,26 +457,17 @@ void launch_rhs(const ProblemDev& P, cudaStream_t st) {
   k_bt_times<<<(P.p * 32 + 255) / 256, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.c, nullptr, P.rhs);
 }
 
-void launch_cholesky(const ProblemDev& P, cudaStream_t st) {
-  // P.v (n >= p entries) holds the original diagonal during the factorisation
-  k_save_diag<<<(P.p + 255) / 256, 256, 0, st>>>(P.A, P.p, P.v);
+void launch_cholesky(const ProblemDev& P, int nb, cudaStream_t st) {
+  k_save_diag<<<dim3((P.p + 255) / 256, nb), 256, 0, st>>>(P.A, P.p, P.diag0);
   for (int j0 = 0; j0 < P.p; j0 += 32) {
-    k_chol_diag<<<1, 32, 0, st>>>(P.A, P.p, j0, P.status, P.v, P.dinv);
+    k_chol_diag<<<dim3(1, nb), 32, 0, st>>>(P.A, P.p, j0, P.status, P.diag0, P.dinv);
     const int m = P.p - j0 - 32;
     if (m > 0) {
-      k_chol_trsm<<<(m + 31) / 32, 32, 0, st>>>(P.A, P.p, j0, P.dinv);
+      k_chol_trsm<<<dim3((m + 31) / 32, nb), 32, 0, st>>>(P.A, P.p, j0, P.dinv);
       const int T = (m + 31) / 32;
-      k_chol_update<<<T * (T + 1) / 2, 256, 0, st>>>(P.A, P.p, j0);
+      k_chol_update<<<dim3(T * (T + 1) / 2, nb), 256, 0, st>>>(P.A, P.p, j0);
     }
   }
-}
-
-void launch_chol_solve(const ProblemDev& P, const double* b, double* x, cudaStream_t st) {
-  // the refinement solve (b == res) adds its correction to x
-  const size_t smem = (size_t)P.p * sizeof(double);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_chol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_chol_solve<<<1, 256, smem, st>>>(P.A, P.p, P.dinv, b, x, b == P.res ? 1 : 0);
 }
 
 void launch_refine_residual(const ProblemDev& P, cudaStream_t st) {

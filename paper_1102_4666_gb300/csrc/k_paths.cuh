@@ -215,7 +215,10 @@ __device__ __forceinline__ void term(const R* __restrict__ tb, int S, int eta, i
 //   1/2 sum_{jl} st_j st_l C_jl d2_jl u
 //     = 1/2 [(1 - rho) sum_j st_j^2 d2_jj u + rho d2_st u],
 // and the diagonal second derivatives come from the few monomials with a
-// repeated variate.  All loop indices are compile-time constants.
+// repeated variate.  Every loop runs over all DP variates with the
+// triangle selected by a test on the indices: the trip counts are then
+// compile-time constants at every nesting level, so the loops unroll
+// completely and the vectors z, zT, bt and st stay in registers.
 template <typename R, int D>
 __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __restrict__ beta,
                                             const R (&z)[D + 1], const R (&zT)[D + 1],
@@ -234,12 +237,14 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
   for (int i = 0; i < DP; ++i) {
     R bv = bg[i], bb = R(0), bs = R(0), bss = R(0), bT = bg[i];
 #pragma unroll
-    for (int j = i; j < DP; ++j) {
+    for (int j = 0; j < DP; ++j) {
+      if (j < i) continue;
       const R q = bq[iq++];
       R av = q, ab = R(0), as = R(0), aT = q;
       if (i == j && i > 0) diag += R(2) * st[i] * st[i] * q;
 #pragma unroll
-      for (int k = j; k < DP; ++k) {
+      for (int k = 0; k < DP; ++k) {
+        if (k < j) continue;
         const R t = bc3[it++];
         av += t * z[k];
         ab += t * bt[k];

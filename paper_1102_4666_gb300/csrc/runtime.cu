@@ -128,9 +128,6 @@ int bsde_set_grid_impl(GridHost& g, int d, int n, const double* lo, const double
 Problem::~Problem() {
   destroy_graph();
   for (auto e : events) cudaEventDestroy(e);
-  if (ev_fork) cudaEventDestroy(ev_fork);
-  if (ev_join) cudaEventDestroy(ev_join);
-  if (side) cudaStreamDestroy(side);
 }
 
 void Problem::destroy_graph() {
@@ -160,8 +157,22 @@ int Problem::choose_launch(int d, int p, int eta, int N, int M, bool mx, bool de
   return BSDE_OK;
 }
 
+int Problem::fact_group(int p, int K_it, bool resample, bool qr) {
+  if (qr || !resample) return 1;
+  const size_t per = fact_block_bytes(p, 1);
+  const size_t cap = (size_t)256 << 20;
+  int g = per > 0 ? (int)(cap / per) : K_it;
+  if (g < 1) g = 1;
+  return g < K_it ? g : K_it;
+}
+
+// A and A^{-1} (p x p each), dinv and the original diagonal (p each), per slot
+size_t Problem::fact_block_bytes(int p, int nfact) {
+  return (size_t)nfact * ((size_t)2 * p * p + (size_t)2 * p) * 8 + 256;
+}
+
 size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int tpb, int ppt, int pm,
-                               int conv_nnz, bool qr) {
+                               int conv_nnz, bool qr, int nfact) {
   (void)N;
   const int n_pad = (n + 31) / 32 * 32;
   const int p_pad = (p + 127) / 128 * 128;
@@ -182,8 +193,6 @@ size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int t
   }
   add((size_t)n * chunks * 8);
   add((size_t)n * 8);
-  add((size_t)p * p * 8);
-  add((size_t)p * p * 8);  // inverse of the Gram matrix
   add((size_t)p * 8 * 4);
   add((size_t)(n > p ? n : p) * 8);
   add((size_t)p * 8);
@@ -205,7 +214,7 @@ size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int t
     add((size_t)p * 8 * 2);
     add((size_t)p * 4 + 16);
   }
-  return b;
+  return b + fact_block_bytes(p, nfact);
 }
 
 int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st) {
@@ -299,15 +308,20 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     s.ppt = prm.paths_ppt;
   }
   s.chunks = (s.M + s.tpb * s.ppt - 1) / (s.tpb * s.ppt);
-  if (!block || !(s == alloc_shape)) {
-    const size_t need = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt, s.pm,
-                                       s.dense ? (int)conv_l.size() : 0, s.qr);
-    if (budget && need > budget) {
+  const int nf = fact_group(p, prm.K_it, grid.resample != 0, s.qr);
+  {
+    const size_t total = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt, s.pm,
+                                        s.dense ? (int)conv_l.size() : 0, s.qr, nf);
+    if (budget && total > budget) {
       std::ostringstream os;
-      os << "solve: needs " << need << " bytes of device memory, budget " << budget;
+      os << "solve: needs " << total << " bytes of device memory, budget " << budget;
       err = os.str();
       return BSDE_ERR_NOMEM;
     }
+  }
+  if (!block || !(s == alloc_shape)) {
+    const size_t need = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt, s.pm,
+                                       s.dense ? (int)conv_l.size() : 0, s.qr, 0);
     destroy_graph();
     if (block) al.put(block, st);
     block = nullptr;
@@ -351,13 +365,10 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     }
     P.partial = (double*)take((size_t)n * s.chunks * 8);
     P.c = (double*)take((size_t)n * 8);
-    P.A = (double*)take((size_t)p * p * 8);
-    P.Ainv = (double*)take((size_t)p * p * 8);
     P.rhs = (double*)take((size_t)p * 8 * 4);
     P.delta = P.rhs + p;
     P.res = P.rhs + 2 * p;
-    P.dinv = P.rhs + 3 * p;
-    P.v = (double*)take((size_t)(n > p ? n : p) * 8);  // also Cholesky scratch (p)
+    P.v = (double*)take((size_t)(n > p ? n : p) * 8);
     P.alpha = (double*)take((size_t)p * 8);
     P.alpha32 = (float*)take((size_t)p * 4);
     P.pairs = (uint2*)take((size_t)p * 8);
@@ -384,6 +395,29 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     }
     dev = P;
     coeffs_valid = false;
+    nfact = 0;  // the factor block is laid out for p again below
+  }
+  // factor block: kept across solves (and across reallocations of the main
+  // block, which do not touch it) while it is large enough
+  const size_t fneed = fact_block_bytes(p, nf);
+  if (!fact || fact_bytes < fneed || nfact != nf || dev.A == nullptr) {
+    if (!fact || fact_bytes < fneed) {
+      destroy_graph();
+      if (fact) al.put(fact, st);
+      fact = al.get(fneed, st);
+      fact_bytes = fact ? fneed : 0;
+      if (!fact) {
+        err = "solve: device allocation failed (Gram factors)";
+        return BSDE_ERR_NOMEM;
+      }
+    }
+    double* f = (double*)fact;
+    const size_t pp = (size_t)p * p;
+    dev.A = f;
+    dev.Ainv = f + (size_t)nf * pp;
+    dev.dinv = f + (size_t)2 * nf * pp;
+    dev.diag0 = dev.dinv + (size_t)nf * p;
+    nfact = nf;
   }
   shape = s;
   dev.chunks = s.chunks;
@@ -424,25 +458,41 @@ static void record(cudaEvent_t e, cudaStream_t st) {
                            cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
+// The Gram matrix of iteration k depends only on the points of iteration k,
+// which depend only on (seed, k): the matrices of a group of iterations are
+// built and factorised together before the group's path kernels, batched
+// over the group (blockIdx.y of the factorisation kernels).  The path kernel
+// then runs alone on the device, and the refit after it is a product with
+// the stored inverse plus FP64 refinement.
+int Problem::enqueue_factors(int k0, int nb, cudaStream_t st) {
+  const size_t pp = (size_t)shape.p * shape.p;
+  for (int j = 0; j < nb; ++j) {
+    const uint32_t kp = grid.resample ? (uint32_t)(k0 + j) : 0u;
+    launch_points(model, grid, dev, kp, st);
+    launch_basis(model, grid, dev, mixed, st);
+    ProblemDev Pj = dev;
+    Pj.A = dev.A + (size_t)j * pp;
+    if (mixed) {
+      const cudaError_t e = launch_gram_tc(Pj, st);
+      if (e != cudaSuccess) {
+        err = std::string("tensor-core Gram launch failed: ") + cudaGetErrorString(e);
+        return BSDE_ERR_CUDA;
+      }
+    } else {
+      launch_gram_f64(Pj, st);
+    }
+  }
+  launch_cholesky(dev, nb, st);
+  launch_inverse(dev, nb, st);
+  return BSDE_OK;
+}
+
 int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t st,
-                               cudaEvent_t* ev) {
+                               cudaEvent_t* ev, int slot) {
   const bool rec = ev != nullptr;
   const uint32_t kp = grid.resample ? (uint32_t)k : 0u;
   launch_points(model, grid, dev, kp, st);
-  launch_basis(model, grid, dev, mixed, st);
-  if (!shape.qr) {
-    if (!side) {
-      int lo = 0, hi = 0;
-      cudaDeviceGetStreamPriorityRange(&lo, &hi);
-      if (cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi) != cudaSuccess ||
-          cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        err = "side stream creation failed";
-        return BSDE_ERR_CUDA;
-      }
-    }
-    cudaEventRecord(ev_fork, st);
-  }
+  launch_basis(model, grid, dev, false, st);  // FP64 B for the refit (no TF32 split)
   if (dev.dense) launch_cheb2mono(dev, st);
   if (rec) record(ev[0], st);
   cudaError_t e = launch_paths(model, grid, dev, shape.M, shape.N, (uint32_t)k, mixed, shape.tpb,
@@ -462,37 +512,15 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
     if (rec) record(ev[4], st);
     launch_qr_solve(dev, st);
   } else {
-    // the Gram matrix, its Cholesky factor and its inverse depend only on
-    // the points: they run on the side stream while the paths run, and the
-    // refit after the paths is a product with the inverse plus FP64
-    // refinement steps against the exact normal equations
-    if (cudaStreamWaitEvent(side, ev_fork, 0) != cudaSuccess) {
-      err = "side stream wait failed";
-      return BSDE_ERR_CUDA;
-    }
-    if (rec) record(ev[3], side);
-    if (mixed) {
-      e = launch_gram_tc(dev, side);
-      if (e != cudaSuccess) {
-        err = std::string("tensor-core Gram launch failed: ") + cudaGetErrorString(e);
-        return BSDE_ERR_CUDA;
-      }
-    } else {
-      launch_gram_f64(dev, side);
-    }
-    if (rec) record(ev[6], side);
-    launch_cholesky(dev, side);
-    launch_inverse(dev, side);
-    if (rec) record(ev[7], side);
-    cudaEventRecord(ev_join, side);
+    ProblemDev Ps = dev;
+    Ps.Ainv = dev.Ainv + (size_t)slot * shape.p * shape.p;
     launch_rhs(dev, st);
-    cudaStreamWaitEvent(st, ev_join, 0);
     if (rec) record(ev[4], st);
-    launch_inv_gemv(dev, dev.rhs, dev.delta, 0, st);
+    launch_inv_gemv(Ps, dev.rhs, dev.delta, 0, st);
     const int refine = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 1);
     for (int r = 0; r < refine; ++r) {
       launch_refine_residual(dev, st);
-      launch_inv_gemv(dev, dev.res, dev.delta, 1, st);
+      launch_inv_gemv(Ps, dev.res, dev.delta, 1, st);
     }
   }
   if (rec) record(ev[5], st);
@@ -506,15 +534,44 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
   return BSDE_OK;
 }
 
+int Problem::enqueue_block(const bsde_solve_params& prm, int k0, int count, cudaStream_t st,
+                           cudaEvent_t* ev) {
+  if (!shape.qr && nfact < 1) {
+    err = "solve: no factor block";
+    return BSDE_ERR_STATE;
+  }
+  int it = 0;
+  while (it < count) {
+    // a group of iterations whose Gram inverses are built first (with fixed
+    // points: one inverse, built once, serves every iteration)
+    const int g = (shape.qr || !grid.resample) ? count - it
+                                               : (nfact < count - it ? nfact : count - it);
+    for (int j = 0; j < g; ++j) {
+      cudaEvent_t* e = ev ? ev + 8 * (it + j) : nullptr;
+      // Gram + factorisation time: events 3 and 7 of the group's first
+      // iteration (zero for the others); the QR refit records its own
+      if (!shape.qr && e) record(e[3], st);
+      if (!shape.qr && j == 0 && (grid.resample || it == 0)) {
+        const int rc = enqueue_factors(k0 + it, grid.resample ? g : 1, st);
+        if (rc != BSDE_OK) return rc;
+      }
+      if (!shape.qr && e) {
+        record(e[6], st);
+        record(e[7], st);
+      }
+      const int rc = enqueue_iteration(prm, k0 + it + j, st, e, grid.resample ? j : 0);
+      if (rc != BSDE_OK) return rc;
+    }
+    it += g;
+  }
+  return BSDE_OK;
+}
+
 int Problem::enqueue_solve(const bsde_solve_params& prm, cudaStream_t st) {
   const int nev = prm.timing ? 8 * prm.K_it : 0;
   if (nev) ensure_events(nev);
-  for (int it = 0; it < prm.K_it; ++it) {
-    const int rc = enqueue_iteration(prm, prm.k_start + it, st,
-                                     nev && (int)events.size() >= nev ? &events[8 * it] : nullptr);
-    if (rc != BSDE_OK) return rc;
-  }
-  return BSDE_OK;
+  return enqueue_block(prm, prm.k_start, prm.K_it, st,
+                       nev && (int)events.size() >= nev ? events.data() : nullptr);
 }
 
 int Problem::start(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st,
@@ -537,7 +594,7 @@ int Problem::start(const bsde_solve_params& prm, Allocator& al, size_t budget, c
     os << shape.d << ' ' << shape.n << ' ' << shape.p << ' ' << shape.M << ' ' << shape.N << ' '
        << prm.K_it << ' ' << prm.k_start << ' ' << prm.refine_steps << ' ' << prm.timing << ' '
        << mixed << ' ' << (void*)block << ' ' << prm.seed << ' ' << prm.eval_mode << ' '
-       << prm.paths_tpb << ' ' << prm.paths_ppt << ' ' << prm.ls_mode;
+       << prm.paths_tpb << ' ' << prm.paths_ppt << ' ' << prm.ls_mode << ' ' << fact << ' ' << nfact;
     if (!gexec || os.str() != graph_key) {
       destroy_graph();
       cudaGraph_t graph = nullptr;
@@ -645,19 +702,27 @@ int Problem::finish_report(const bsde_solve_params& prm, cudaStream_t st, bsde_r
     r.path_steps_per_s = ms_total > 0 ? r.path_steps / (ms_total * 1e-3) : 0.0;
     r.path_launches = prm.K_it;
     r.rank = rank;
+    // launches: per iteration points, basis, (monomial conversion), paths,
+    // reduce, refit (QR: init, pivot + apply per step, solve; otherwise
+    // rhs, inverse product, 3 per refinement step), update, read-out (3);
+    // per factorised Gram matrix points, basis, Gram (+ split-K reduce in
+    // mixed precision); per group save_diag, 3 per panel but the last
+    // (diag, trsm, update), the last panel's diag, the batched inverse
     const int panels = (shape.p + 31) / 32;
-    const int chol = 1 + 3 * panels - 2;
     const int steps_qr = shape.p < shape.n ? shape.p : shape.n;
     const int refine2 = prm.refine_steps >= 0 ? prm.refine_steps : (mixed ? 2 : 1);
-    const int refit = shape.qr ? (2 + 2 * steps_qr)
-                               : ((mixed ? 2 : 1) + 1 + chol + 1 + 1 + refine2 * 3);
-    r.kernel_launches = prm.K_it * (2 + (dev.dense ? 1 : 0) + 1 + 1 + refit + 1 + 3);
-    // points, basis, paths, reduce, Gram (+ reduce), rhs, Cholesky, solve,
-    // refinement (2 GEMVs + solve each), update, read-out (3)
+    const int refit = shape.qr ? (2 + 2 * steps_qr) : (2 + 3 * refine2);
+    int groups = 0, mats = 0;
+    if (!shape.qr) {
+      groups = grid.resample ? (prm.K_it + nfact - 1) / nfact : 1;
+      mats = grid.resample ? prm.K_it : 1;
+    }
+    r.kernel_launches = prm.K_it * (2 + (dev.dense ? 1 : 0) + 1 + 1 + refit + 1 + 3) +
+                        mats * (2 + (mixed ? 2 : 1)) + groups * (3 * panels - 1 + 1);
     if (prm.timing && (int)events.size() >= 8 * prm.K_it) {
-      // paths: ev0..ev1; Gram (side stream): ev3..ev6; factor + inverse
-      // (side stream, overlapped with the paths) ev6..ev7 are counted in the
-      // Gram figure; critical-path refit after the paths: ev4..ev5
+      // paths: ev0..ev1; Gram matrices, factors and inverses built ahead of
+      // a group of iterations: ev3..ev7 of the group's first iteration;
+      // refit after the paths: ev4..ev5
       double mp = 0, mg = 0, msv = 0;
       for (int k = 0; k < prm.K_it; ++k) {
         cudaEvent_t* e = &events[8 * k];
@@ -681,6 +746,11 @@ void Problem::release(Allocator& al, cudaStream_t st) {
   if (block) al.put(block, st);
   block = nullptr;
   block_bytes = 0;
+  if (fact) al.put(fact, st);
+  fact = nullptr;
+  fact_bytes = 0;
+  nfact = 0;
+  dev = ProblemDev();
   alloc_shape = Shape();
   coeffs_valid = false;
 }

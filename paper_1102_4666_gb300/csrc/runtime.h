@@ -51,8 +51,11 @@ class Problem {
   ~Problem();
   // validate params, build the basis, (re)allocate device memory; BSDE_OK or an error
   int prepare(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st);
-  // launch one iteration k -> k+1 (no synchronisation)
-  int enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t st, cudaEvent_t* ev);
+  // launch iterations k0 .. k0 + count - 1 (no synchronisation), each
+  // group of them after the factorisation of its Gram matrices; ev: 8
+  // timing events per iteration or nullptr
+  int enqueue_block(const bsde_solve_params& prm, int k0, int count, cudaStream_t st,
+                    cudaEvent_t* ev);
   // full solve: alpha reset (k_start == 0), K_it iterations, report
   int solve(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st,
             bsde_report* rep);
@@ -67,25 +70,36 @@ class Problem {
                     float ms_total);
   void release(Allocator& al, cudaStream_t st);
   void destroy_graph();  // after a model or grid change
-  size_t bytes() const { return block_bytes; }
+  size_t bytes() const { return block_bytes + fact_bytes; }
   static size_t estimate_bytes(int d, int n, int p, int M, int N, bool mixed, int tpb, int ppt,
-                               int pm = 0, int conv_nnz = 0, bool qr = false);
+                               int pm = 0, int conv_nnz = 0, bool qr = false, int nfact = 1);
+  // Gram matrices factorised together ahead of their iterations: all K_it
+  // of a solve while their factors and inverses fit in 256 MiB (one when
+  // the points are not redrawn, none for the QR refit)
+  static int fact_group(int p, int K_it, bool resample, bool qr);
+  static size_t fact_block_bytes(int p, int nfact);
 
  private:
   void* block = nullptr;
   size_t block_bytes = 0;
   Shape alloc_shape;
+  // Gram matrices, Cholesky factors and inverses of up to nfact iterations
+  void* fact = nullptr;
+  size_t fact_bytes = 0;
+  int nfact = 0;
   // graph of a whole solve
   cudaGraphExec_t gexec = nullptr;
   std::string graph_key;
-  std::vector<cudaEvent_t> events;  // 6 per iteration when timing
-  // side stream of the overlapped refit: the Gram matrix, its factor and its
-  // inverse depend only on the points, so they run while the paths run
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<cudaEvent_t> events;  // 8 per iteration when timing
   int choose_launch(int d, int p, int eta, int N, int M, bool mixed, bool dense, int& tpb,
                     int& ppt);
   void ensure_events(int count);
+  // points, basis and Gram matrix of iterations k0 .. k0 + nb - 1 into the
+  // nb slots of the factor block, then their batched factorisation and inverses
+  int enqueue_factors(int k0, int nb, cudaStream_t st);
+  // one iteration k -> k + 1 whose Gram inverse is in slot `slot`
+  int enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t st, cudaEvent_t* ev,
+                        int slot);
 };
 
 int bsde_set_model_impl(ModelHost& m, const bsde_sigma* sigma, double r, const bsde_payoff* payoff,

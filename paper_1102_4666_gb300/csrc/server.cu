@@ -211,8 +211,10 @@ int bsde_server_submit(bsde_server* s, const bsde_request* rq, uint64_t* id) {
     rc = bsde_basis_size(r->model.d, r->prm.eta, r->prm.q, &p);
     if (rc != BSDE_OK) return rc;
     const int tpb = s->opts.precision == BSDE_PREC_MIXED ? 128 : 64;
+    const bool qr = r->prm.ls_mode == 1;
     r->bytes = Problem::estimate_bytes(r->model.d, rq->n, p, r->prm.M, r->prm.N_steps,
-                                       s->opts.precision == BSDE_PREC_MIXED, tpb, 4);
+                                       s->opts.precision == BSDE_PREC_MIXED, tpb, 4, 0, 0, qr,
+                                       Problem::fact_group(p, r->prm.K_it, true, qr));
     r->work = (double)r->prm.K_it * rq->n * (double)r->prm.M * r->prm.N_steps;
     r->t_submit = now_s();
     std::lock_guard<std::mutex> g(s->mu);
