@@ -29,19 +29,22 @@ METRIC = "path-steps/s incl. u^k,∇u^k,Lu^k eval at d=10 (vs FP64 plain); p50/p
 UNIT = "path-steps/s"
 CONFIG = "c4"
 
-# FP32 arithmetic of one path-step of the d = 10 kernel, counted from the
-# source (an FMA counts 2): correlation L Z 100, local volatility 10 x 8,
-# drift and update 10 x 7, Box-Muller 5 pairs x 10 -> 300.  The per-path
-# evaluation of u^k and its derivatives (~11k flops for p = 364) adds
-# ~110 per step at N = 100; only the 300 of the Euler step are counted.
+# Algorithmic FP32 work of one Euler path-step at d = 10 (an FMA counts 2),
+# for the plain formulation of the step, rounded: correlation L Z as a
+# triangular product (55 multiply-adds, ~100), local volatility 10 x 8,
+# drift and update 10 x 7, Box-Muller 5 pairs x 10 -> ~300.  The kernel executes fewer FP32 operations than this
+# (prefix sums for the constant correlation, tabulated volatility
+# coefficients, one Box-Muller radius factor); the per-path evaluation of
+# u^k and its derivatives (~11k flops for p = 364, ~110 per step at N = 100)
+# is not counted.
 FLOPS_PER_PATH_STEP = 300.0
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of one path-kernel launch per point, from the ncu
-# capture summarised in profiles/k_paths_d10_dense_n800.md, scaled to a
+# capture summarised in profiles/k_paths_d10_dense_n800.md (n = 800 points:
+# 149.2 KB read, 0 B written: the partial sums stay in L2), scaled to a
 # launch over n points (the kernel reads the points and coefficients and
-# writes one partial sum per (point, chunk), both proportional to n).  None
-# while the kernel has changed since the capture.
-PATH_TRAFFIC_BYTES_PER_POINT = None
+# writes one partial sum per (point, chunk), both proportional to n).
+PATH_TRAFFIC_BYTES_PER_POINT = (149248.0 + 0.0) / 800.0
 
 
 def env_rank():
@@ -94,6 +97,16 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+
+    def wait_ready(self, samples=3, timeout_s=30.0):
+        """Block until nvidia-smi delivers samples: its start-up (NVML
+        initialisation, seconds on a fresh machine) must not overlap the
+        timed region."""
+        t0 = time.perf_counter()
+        while self.proc is not None and len(self.lines) < samples:
+            if time.perf_counter() - t0 > timeout_s or self.proc.poll() is not None:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -197,15 +210,10 @@ def run_profile_case(args):
     return 0
 
 
-def run_serving(n_requests, precision="mixed", slots=16, seed=7, load=0.8, policy="fifo"):
-    """Continuous-batching serving mix: a seeded Poisson stream of pricing
-    requests of uneven d, n, M and degree (workloads.serving_mix) submitted
-    at their arrival times to bsde_server; arrival rate calibrated to `load`
-    times the measured capacity.  Returns p50/p99 latency and throughput."""
+def serving_capacity(reqs, slots=16, precision="mixed"):
+    """Path-steps/s of a warm server running the first requests of the mix
+    back to back."""
     import paper_1102_4666_gb300 as G
-    reqs = workloads.serving_mix(n_requests, seed=seed)
-    mean_steps = sum(workloads.path_steps(r) for r in reqs) / len(reqs)
-    # capacity: a few requests back to back on a warm server
     srv = G.Server(max_slots=slots, precision=precision)
     calib = reqs[:min(16, len(reqs))]
     t0 = time.perf_counter()
@@ -214,16 +222,28 @@ def run_serving(n_requests, precision="mixed", slots=16, seed=7, load=0.8, polic
     el = time.perf_counter() - t0
     for i in ids:
         srv.poll(i)
-    cap = sum(workloads.path_steps(r) for r in calib) / el
     srv.close()
-    rate = load * cap / mean_steps
+    return sum(workloads.path_steps(r) for r in calib) / el
+
+
+def arrival_times(n, rate_hz, seed):
     rng = __import__("random").Random(seed)
+    t, out = 0.0, []
+    for _ in range(n):
+        t += rng.expovariate(rate_hz)
+        out.append(t)
+    return out
+
+
+def run_serving(reqs, arrivals, precision="mixed", slots=16, policy="fifo"):
+    """Continuous-batching serving: the requests of the mix submitted to
+    bsde_server at their arrival times (seconds from the start).  Returns
+    p50/p99 latency (submit to completion) and throughput."""
+    import paper_1102_4666_gb300 as G
     srv = G.Server(max_slots=slots, precision=precision, policy=policy)
     t_start = time.perf_counter()
-    t_arr = 0.0
     ids = []
-    for r in reqs:
-        t_arr += rng.expovariate(rate)
+    for r, t_arr in zip(reqs, arrivals):
         now = time.perf_counter() - t_start
         if t_arr > now:
             time.sleep(t_arr - now)
@@ -238,10 +258,63 @@ def run_serving(n_requests, precision="mixed", slots=16, seed=7, load=0.8, polic
             bad += 1
     srv.close()
     return {"requests": len(reqs), "precision": precision, "slots": slots, "policy": policy,
-            "arrival_rate_hz": rate, "calibrated_capacity_path_steps_per_s": cap, "load": load,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "path_steps_per_s": st["path_steps"] / wall, "busy_path_steps_per_s": st["path_steps_per_s"],
             "wall_s": wall, "failed": bad}
+
+
+def fp64_sequential_model(reqs, arrivals):
+    """The plain comparator for serving: one request at a time in FP64 on
+    the GPU, FIFO.  Its service rate is measured per number of assets d on
+    one FP64 iteration of the first request with that d (M capped at 1000);
+    each request's service time is its path-steps at that rate, and the
+    latencies follow from the same arrival times through a single FIFO
+    server.  Simulating the queue instead of running it keeps the bench
+    short: the FP64 path needs minutes for this mix."""
+    import numpy as np
+    import paper_1102_4666_gb300 as G
+    rates = {}
+    for r in reqs:
+        if r["d"] in rates:
+            continue
+        probe = dict(r)
+        probe["K_it"] = 1
+        probe["M"] = min(r["M"], 1000)
+        s = G.Solver(probe, precision="fp64")
+        s.solve(use_graph=0, K_it=1)
+        rep = s.solve(use_graph=0, K_it=1, timing=1)
+        s.close()
+        rates[r["d"]] = rep.path_steps / (rep.ms_total * 1e-3)
+    t_free, lat = 0.0, []
+    for r, t_arr in zip(reqs, arrivals):
+        start = max(t_arr, t_free)
+        t_free = start + workloads.path_steps(r) / rates[r["d"]]
+        lat.append((t_free - t_arr) * 1e3)
+    lat = np.array(lat)
+    total = sum(workloads.path_steps(r) for r in reqs)
+    return {"precision": "fp64", "slots": 1, "policy": "fifo", "kind": "modeled from measured FP64 rates",
+            "fp64_path_steps_per_s_by_d": {str(k): v for k, v in sorted(rates.items())},
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "path_steps_per_s": total / (t_free - 0.0)}
+
+
+def run_serving_suite(n_requests, seed=7, load=0.8):
+    """One seeded request mix and one arrival stream (rate: `load` times the
+    16-slot capacity), served four ways: FIFO and shortest-first with 16
+    slots, FIFO with one slot (one request at a time, mixed precision), and
+    the modeled one-at-a-time FP64 comparator."""
+    reqs = workloads.serving_mix(n_requests, seed=seed)
+    mean_steps = sum(workloads.path_steps(r) for r in reqs) / len(reqs)
+    cap = serving_capacity(reqs)
+    rate = load * cap / mean_steps
+    arr = arrival_times(len(reqs), rate, seed)
+    out = {"arrival_rate_hz": rate, "calibrated_capacity_path_steps_per_s": cap, "load": load,
+           "requests": len(reqs)}
+    out["fifo"] = run_serving(reqs, arr, slots=16, policy="fifo")
+    out["shortest_first"] = run_serving(reqs, arr, slots=16, policy="shortest")
+    out["one_at_a_time_mixed"] = run_serving(reqs, arr, slots=1, policy="fifo")
+    out["one_at_a_time_fp64"] = fp64_sequential_model(reqs, arr)
+    return out
 
 
 def run_ours(args):
@@ -272,7 +345,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(1.0)  # let nvidia-smi start before the timed region
+    clocks.wait_ready()  # nvidia-smi running before the timed region
     reps = []
     if world > 1:
         torch.distributed.barrier()
@@ -341,9 +414,7 @@ def run_ours(args):
     launch_steps = cfg["n"] * cfg["M"] * cfg["N"]
     achieved = FLOPS_PER_PATH_STEP * launch_steps / (path_ms * 1e-3) / 1e12 if path_ms > 0 else None
     cpu = cpu_oracle_rate(cfg, budget_s=args.cpu_budget) if not args.no_cpu else None
-    serving = run_serving(args.serving_requests) if args.serving_requests > 0 else None
-    serving_sjf = (run_serving(args.serving_requests, slots=4, policy="shortest")
-                   if args.serving_requests > 0 else None)
+    serving = run_serving_suite(args.serving_requests) if args.serving_requests > 0 else None
     rep0 = reps[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -369,6 +440,7 @@ def run_ours(args):
         "fp64_plain": fp64,
         "solve": {"price": rep0.price, "delta0": rep0.delta[0], "ms_paths": rep0.ms_paths,
                   "ms_gram": rep0.ms_gram, "ms_solve": rep0.ms_solve, "ms_total": rep0.ms_total,
+                  "ms_total_timed_steps": [r.ms_total for r in reps],
                   "resid_l2_first_last": [rep0.resid_l2[0], rep0.resid_l2[cfg["K_it"] - 1]],
                   "note": "penalty lambda T = 100 is far outside the range where the Picard "
                           "iteration contracts (error bound (lambda T)^k / k!): the iterates of this "
@@ -376,7 +448,6 @@ def run_ours(args):
         "solve_omega1": omega1,
         "cpu_baseline": cpu,
         "serving": serving,
-        "serving_shortest_first": serving_sjf,
     }
     print(json.dumps(line))
     if world > 1:

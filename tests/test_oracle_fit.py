@@ -106,3 +106,52 @@ def test_european_solve_approaches_black_scholes():
     assert all(abs(p - bs) < 0.04 * bs for p in prices)
     assert abs(np.mean(prices) - bs) < 0.02 * bs
     assert all(abs(h["delta"][0] - bsd) < 0.02 for h in res["history"][1:])
+
+
+def _put_d1(lam, r, S0, K_it):
+    return workloads.make(d=1, T=1.0, r=r, K=100.0, S0=S0, vol={"kind": "const", "a": 0.2},
+                          rho=0.0, lam=lam, n=600, M=4000, N=10, eta=6, K_it=K_it, seed=21,
+                          half_width=1.0)
+
+
+def test_picard_residual_decreases():
+    """The Picard map of Algorithm 2 contracts: with the driver's Lipschitz
+    constant omega, the error after k iterations is bounded by
+    (omega T)^k / k! times the first one (plus the Monte Carlo and
+    projection floor).  European put (omega = 0): the second step is already
+    at the floor, far below the first.  Penalised put with the paper's
+    omega = 1: the steps shrink one after the other before reaching it."""
+    eu = O.solve(_put_d1(0.0, 0.02, 100.0, 3))["history"]
+    assert eu[1]["resid_l2"] < 0.1 * eu[0]["resid_l2"]
+    assert eu[2]["resid_l2"] < 0.1 * eu[0]["resid_l2"]
+    am = O.solve(_put_d1(1.0, 0.1, 90.0, 4))["history"]
+    r = [h["resid_l2"] for h in am]
+    assert r[0] > r[1] > r[2] > r[3]
+    assert r[3] < 0.1 * r[0]
+
+
+def test_penalised_price_lies_between_european_and_american():
+    """The penalised BSDE (eq. bsde-penal-2) adds omega (Phi - Y)^+ >= 0 to
+    the European driver and its solution increases to the American price as
+    omega grows (Section 4.3), so for omega = 1:
+    BS European <= Y^omega <= American (CRR tree, 2000 steps).  With
+    r = 0.1 and S0 = 90 the bracket is wide (7.43 .. 10.43); the mean of the
+    converged iterates also matches the finite-difference solution of the
+    penalised PDE (8.46) within 10 % (Monte Carlo noise of four iterates,
+    the degree-6 projection and the 10-step time grid: 8.96 here)."""
+    res = O.solve(_put_d1(1.0, 0.1, 90.0, 8))
+    prices = np.array([h["price"] for h in res["history"][4:]])
+    eu = CF.bs_put(90.0, 100.0, 0.1, 0.2, 1.0)
+    am = CF.crr_put(90.0, 100.0, 0.1, 0.2, 1.0, 2000, True)
+    fd = CF.fd_penalised_put(90.0, 100.0, 0.1, lambda t, x: 0.2, 1.0, 1.0, nx=400, nt=200)
+    assert np.all(prices > eu) and np.all(prices < am)
+    assert abs(prices.mean() - fd) < 0.10 * fd
+
+
+def test_penalised_limit_dominates_the_payoff():
+    """The American price (the limit of the penalised solutions) is at least
+    the payoff: the finite-difference penalised put at omega = 1000 is above
+    max(K - S, 0) up to its O(1/omega) penalty gap, at, in and out of the money."""
+    for S in (60.0, 80.0, 90.0, 100.0, 120.0):
+        p = CF.fd_penalised_put(S, 100.0, 0.1, lambda t, x: 0.2, 1.0, 1000.0, nx=400, nt=200)
+        assert p >= max(100.0 - S, 0.0) - 0.05
