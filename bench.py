@@ -341,6 +341,8 @@ def run_ours(args):
         return s.solve(use_graph=1, timing=timing)
 
     for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # also loads the fill kernel's module before the timed region
         step()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
