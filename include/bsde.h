@@ -22,7 +22,8 @@
  *     the caller; the library copies what it needs before returning.
  *   - Device memory is owned by the context and released by bsde_destroy();
  *     it comes from the caller's allocation hooks when given (for example
- *     PyTorch's caching allocator), else from cudaMalloc.
+ *     PyTorch's caching allocator), else from a stream-ordered memory pool
+ *     of the library (allocated and freed on the context's stream).
  *   - Calls on one context must not overlap (one host thread at a time).
  *   - Requires an sm_103a GPU; without one bsde_create() returns
  *     BSDE_ERR_CUDA.
@@ -86,7 +87,8 @@ typedef struct {
   int device;           /* CUDA device ordinal                                */
   void* stream;         /* cudaStream_t to work on; NULL: the library creates
                            its own non-blocking stream                        */
-  bsde_alloc_fn alloc;  /* optional device allocator (NULL: cudaMalloc)        */
+  bsde_alloc_fn alloc;  /* optional device allocator (NULL: a stream-ordered
+                           memory pool of the library, cudaMallocFromPoolAsync) */
   bsde_free_fn free;    /* its release function (required with alloc)          */
   void* alloc_user;     /* passed back to alloc/free                           */
   size_t mem_budget;    /* bytes of device memory the context may hold; 0 = no
@@ -305,6 +307,12 @@ typedef struct bsde_server bsde_server;
 #define BSDE_POLICY_FIFO 0     /* admit in arrival order                        */
 #define BSDE_POLICY_SHORTEST 1 /* admit the queued request with the fewest
                                   path-steps (K_it n M N) first             */
+#define BSDE_POLICY_RESPONSE_RATIO 2 /* admit the queued request with the
+                                  highest (wait + service) / service, the
+                                  service time estimated from its path-steps
+                                  and the server's measured throughput: short
+                                  requests go first, long ones rise as they
+                                  wait (no starvation)                      */
 
 typedef struct {
   int device;

@@ -418,7 +418,7 @@ class Server:
     def __init__(self, device=0, max_slots=16, mem_budget=0, precision="mixed", policy="fifo"):
         o = bsde_server_opts()
         o.device, o.max_slots, o.mem_budget = device, max_slots, mem_budget
-        o.policy = 1 if policy == "shortest" else 0
+        o.policy = {"fifo": 0, "shortest": 1, "response_ratio": 2}[policy]
         o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
         h = ctypes.c_void_p()
         rc = lib().bsde_server_create(ctypes.byref(h), ctypes.byref(o))

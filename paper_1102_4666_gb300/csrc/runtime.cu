@@ -3,14 +3,53 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <sstream>
 
 #include "multiindex.h"
 
+// Without caller hooks, memory comes from a library-private stream-ordered
+// pool per device: cudaFree would synchronise the whole device, which in the
+// serving loop stalls every resident request at each completion.  The pool
+// keeps up to 2 GiB of freed memory for reuse.
+namespace {
+constexpr int POOL_DEVICES = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[POOL_DEVICES] = {};
+bool g_pool_tried[POOL_DEVICES] = {};
+
+cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= POOL_DEVICES) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_pool_tried[dev]) {
+    g_pool_tried[dev] = true;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&g_pool[dev], &props) != cudaSuccess) {
+      cudaGetLastError();
+      g_pool[dev] = nullptr;
+    } else {
+      uint64_t keep = (uint64_t)2 << 30;
+      cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
+  return g_pool[dev];
+}
+}  // namespace
+
 void* Allocator::get(size_t bytes, cudaStream_t st) {
   if (alloc) return alloc(bytes, (void*)st, user);
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  cudaMemPool_t pool = device_pool();
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -21,6 +60,8 @@ void Allocator::put(void* p, cudaStream_t st) {
   if (!p) return;
   if (alloc) {
     if (free) free(p, (void*)st, user);
+  } else if (device_pool()) {
+    cudaFreeAsync(p, st);
   } else {
     cudaFree(p);
   }

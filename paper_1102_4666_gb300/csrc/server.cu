@@ -73,11 +73,28 @@ struct bsde_server {
 
 bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
   if (queue.empty() || (int)running.size() >= opts.max_slots) return false;
-  // next request: the oldest (FIFO) or the one with the least work
+  // next request: the oldest (FIFO), the one with the least work, or the
+  // one with the highest response ratio (wait + service) / service
   size_t pick = 0;
-  if (opts.policy == BSDE_POLICY_SHORTEST)
+  if (opts.policy == BSDE_POLICY_SHORTEST) {
     for (size_t q = 1; q < queue.size(); ++q)
       if (queue[q]->work < queue[pick]->work) pick = q;
+  } else if (opts.policy == BSDE_POLICY_RESPONSE_RATIO) {
+    // service estimate: path-steps at the throughput measured so far (a
+    // GB300-scale default until a second of busy time has been seen)
+    const double t = now_s();
+    const double busy = busy_s + (busy_since >= 0 ? t - busy_since : 0.0);
+    const double rate = busy > 1.0 && path_steps > 0 ? path_steps / busy : 5e10;
+    double best = -1.0;
+    for (size_t q = 0; q < queue.size(); ++q) {
+      const double svc = queue[q]->work / rate + 1e-4;
+      const double ratio = (t - queue[q]->t_submit + svc) / svc;
+      if (ratio > best) {
+        best = ratio;
+        pick = q;
+      }
+    }
+  }
   Req* r = queue[pick].get();
   if (opts.mem_budget && used_bytes + r->bytes > opts.mem_budget && !running.empty()) return false;
   std::unique_ptr<Req> req = std::move(queue[pick]);
@@ -175,7 +192,8 @@ extern "C" {
 int bsde_server_create(bsde_server** out, const bsde_server_opts* o) {
   if (!out || !o || o->max_slots < 1 || o->max_slots > 64 ||
       (o->precision != BSDE_PREC_FP64 && o->precision != BSDE_PREC_MIXED) ||
-      (o->policy != BSDE_POLICY_FIFO && o->policy != BSDE_POLICY_SHORTEST))
+      (o->policy != BSDE_POLICY_FIFO && o->policy != BSDE_POLICY_SHORTEST &&
+       o->policy != BSDE_POLICY_RESPONSE_RATIO))
     return BSDE_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o->device < 0 || o->device >= ndev) {

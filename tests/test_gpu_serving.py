@@ -97,3 +97,11 @@ def test_shortest_first_policy_overtakes_queued_long_requests():
     order = _completion_order("shortest")
     assert sorted(order) == [0, 1, 2]
     assert order.index(2) < order.index(1)
+
+
+def test_response_ratio_policy_serves_short_first_and_everyone():
+    """Highest response ratio next: the short request queued behind a long
+    one goes first (its ratio grows fastest), and every request completes."""
+    order = _completion_order("response_ratio")
+    assert sorted(order) == [0, 1, 2]
+    assert order.index(2) < order.index(1)
