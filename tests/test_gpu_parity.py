@@ -190,16 +190,23 @@ def test_refit_solves_the_normal_equations(G, prec):
     assert rel(a1 - a0, delta) < 1e-9
 
 
-@pytest.mark.parametrize("ev", [0, 1])
-def test_full_size_c4_sampled_points(G, ev):
+# the launch shapes the autotuner can give bench.py (dense evaluation), and
+# the library's default shape for the per-thread-table evaluation
+_FULL_SIZE = [(0, shape) for shape in __import__(
+    "paper_1102_4666_gb300.autotune", fromlist=["CANDIDATES"]).CANDIDATES["mixed"]] + [(1, None)]
+
+
+@pytest.mark.parametrize("ev,shape", _FULL_SIZE)
+def test_full_size_c4_sampled_points(G, ev, shape):
     """c4 at its full size (n=4000, M=4000, N=100, p=364), one mixed
-    iteration in the bench's launch configuration; the oracle recomputes
-    c_i at a sample of points."""
+    iteration in each launch configuration bench.py can time (threads per
+    CTA x paths per thread); the oracle recomputes c_i at a sample of points."""
     cfg = workloads.config("c4")
     nu = O.multi_index_set(11, 3)
     a0 = _alpha(cfg, nu, scale=1.0)
     s = solver(G, cfg, "mixed")
-    t, x, c, a1 = s.iterate(5, a0, eval_mode=ev)
+    kw = {} if shape is None else {"paths_tpb": shape[0], "paths_ppt": shape[1]}
+    t, x, c, a1 = s.iterate(5, a0, eval_mode=ev, **kw)
     s.close()
     idx = np.arange(0, 4000, 500)
     co = O.correction(cfg, nu, a0, 5, idx, t[idx], x[:, idx], nthreads=NTH)
