@@ -104,6 +104,10 @@ CASES = {
     "d3_call": ("c3", dict(d=3, n=90, M=130, N=9, eta=3, payoff="call")),
     "d10_tail": ("c4", dict(n=200, M=33, N=7, eta=2)),
     "d1_raw_obstacle": ("c2", dict(n=120, M=200, N=13, eta=5, obstacle="raw")),
+    # degenerate sizes: one Euler step and one path per point; an odd step
+    # count (the last group of two steps is half full) and a few paths
+    "d10_one_step_one_path": ("c4", dict(n=160, M=1, N=1, eta=2)),
+    "d5_odd_steps": ("c3", dict(n=60, M=5, N=3, eta=2)),
 }
 
 
@@ -273,6 +277,28 @@ def test_graph_and_direct_launch_agree_and_are_deterministic(G):
     s.close()
     assert np.array_equal(a1, a2) and np.array_equal(a1, a3)
     assert r1.price == r2.price == r3.price
+
+
+def test_library_memory_pool_matches_caller_allocator(G):
+    """Without allocation hooks the context takes its memory from the
+    library's stream-ordered pool; results are those of a context on
+    PyTorch's caching allocator, also after the factor block is laid out
+    again for a different number of iterations and after one iteration
+    through bsde_iterate."""
+    cfg = workloads.config("c4", n=200, M=300, N=10, K_it=3, eta=2)
+    out = []
+    for torch_memory in (True, False):
+        s = G.Solver(cfg, precision="mixed", torch_memory=torch_memory)
+        r3 = s.solve(use_graph=1)
+        r5 = s.solve(use_graph=1, K_it=5)
+        a5 = s.coeffs()
+        _, _, c1, a1 = s.iterate(1)
+        r3b = s.solve(use_graph=1)
+        s.close()
+        out.append((r3.price, r5.price, a5, c1, a1, r3b.price))
+    (p3, p5, a5, c1, a1, p3b), (q3, q5, b5, d1, b1, q3b) = out
+    assert p3 == q3 == p3b == q3b and p5 == q5
+    assert np.array_equal(a5, b5) and np.array_equal(c1, d1) and np.array_equal(a1, b1)
 
 
 def test_checkpoint_resume_reproduces_the_run(G):
