@@ -416,6 +416,17 @@ def run_ours(args):
     chk.close()
     omega1 = {"lambda": 1.0, "price": r1.price, "delta": list(r1.delta[:10]),
               "resid_l2": list(r1.resid_l2[:cfg["K_it"]]), "status": r1.status}
+    # the other configured workloads (whole solves, graph replay, device time)
+    others = {}
+    for name, prec in (("c1", "fp64"), ("c2", "mixed"), ("c3", "mixed")):
+        wc = workloads.config(name)
+        ws = G.Solver(wc, precision=prec, device=local)
+        ws.solve(use_graph=1)
+        best = min((ws.solve(use_graph=1) for _ in range(3)), key=lambda r: r.ms_total)
+        ws.close()
+        others[name] = {"workload": wc["name"], "precision": prec, "p": best.p,
+                        "path_steps": best.path_steps, "ms_per_solve": best.ms_total,
+                        "path_steps_per_s": best.path_steps_per_s}
     sm_mhz = clk.get("sm_mhz") or 2070.0
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     launch_steps = cfg["n"] * cfg["M"] * cfg["N"]
@@ -453,6 +464,7 @@ def run_ours(args):
                           "iteration contracts (error bound (lambda T)^k / k!): the iterates of this "
                           "throughput workload grow over its 12 iterations; see solve_omega1"},
         "solve_omega1": omega1,
+        "other_workloads": others,
         "cpu_baseline": cpu,
         "serving": serving,
     }

@@ -166,9 +166,11 @@ struct ProblemDev {
   uint32_t seed_key[2] = {0, 0};  // the same key on the host, a parameter of the path kernel
   int* status = nullptr;      // [1] device status bits
   double* out = nullptr;      // report block (see OUT_* offsets)
-  // dense evaluation (basis of total degree <= 3): monomial coefficients
+  // dense evaluation (basis of total degree <= 3, or <= 4 for d <= 5):
+  // monomial coefficients
   bool dense = false;
-  int pm = 0;                 // number of monomials, C(d + 4, 3)
+  bool dense4 = false;        // monomials up to degree 4
+  int pm = 0;                 // number of monomials, C(d + 4, 3) or C(d + 5, 4)
   double* beta = nullptr;     // [pm]
   float* beta32 = nullptr;    // [pm]
   int* conv_row = nullptr;    // [pm + 1] CSR rows of the Chebyshev -> monomial map

@@ -16,10 +16,11 @@
 // the main loop only records the states before and after step s* (for the
 // Chebyshev-table kernels behind a warp vote, so that a warp none of whose
 // paths is at its step s* skips the copies), and X_tau is drawn after the
-// loop through a Brownian bridge.  u^k and its derivatives at (tau, X_tau) and u^k(T, X_T) come
-// from per-thread Chebyshev tables in shared memory (layout [slot][thread],
-// conflict-free), or, when the basis has total degree <= 3 (EV = EV_DENSE3),
-// from the monomial coefficients beta of u^k (converted from the Chebyshev
+// loop through a Brownian bridge.  u^k and its derivatives at (tau, X_tau)
+// and u^k(T, X_T) come from per-thread Chebyshev tables in shared memory
+// (layout [slot][thread], conflict-free), or, when the basis has total
+// degree <= 3 (EV = EV_DENSE3; <= 4 for d <= 5, EV = EV_DENSE4), from the
+// monomial coefficients beta of u^k (converted from the Chebyshev
 // coefficients once per iteration) by unrolled symmetric-tensor loops whose
 // indices are compile-time constants, so that u, grad u and the Hessian stay
 // in registers.  Per-path samples are accumulated in FP64; the CTA
@@ -33,7 +34,7 @@ namespace paths {
 // volatility families: constant, a + phi(t) tanh(x - kappa) (sin/tanh),
 // Dupire's, and a + phi(t) |tanh(x - kappa)| (abs/tanh)
 enum { VK_CONST = 0, VK_TANH = 1, VK_DUPIRE = 2, VK_TANH_ABS = 3 };
-enum { EV_TABLES = 0, EV_DENSE3 = 1 };
+enum { EV_TABLES = 0, EV_DENSE3 = 1, EV_DENSE4 = 2 };
 
 // monomials of total degree <= 3 in dp variates: C(dp + 3, 3)
 __host__ __device__ constexpr int ncubic(int dp) { return (dp + 3) * (dp + 2) * (dp + 1) / 6; }
@@ -286,6 +287,116 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
   gen = ub + R(0.5) * ((R(1) - a.rho) * diag + a.rho * uss);
 }
 
+// The same for a basis of total degree <= 4 (d <= 5), one more Horner level:
+//   u = c + sum_i z_i (g_i + sum_{j>=i} z_j (q_ij + sum_{k>=j} z_k (t_ijk
+//         + sum_{l>=k} f_ijkl z_l))),
+// monomials ordered constant, linear, quadratic, cubic, quartic, each group
+// lexicographic.  The weighted Hessian diagonal sum_v st_v^2 d2_vv u takes,
+// from each monomial with a variate v repeated e >= 2 times, e (e - 1)
+// st_v^2 times the product of its other factors; the index patterns are
+// compile-time constants, so each coefficient gets only its own terms.
+template <typename R, int D>
+__device__ __forceinline__ void eval_dense4(const Args<R, D>& a, const R* __restrict__ beta,
+                                            const R (&z)[D + 1], const R (&zT)[D + 1],
+                                            const R (&bt)[D + 1], const R (&st)[D + 1], R& u,
+                                            R& gen, R& uT) {
+  constexpr int DP = D + 1;
+  constexpr int NQ = DP * (DP + 1) / 2;
+  constexpr int NC = DP * (DP + 1) * (DP + 2) / 6;
+  const R* bg = beta + 1;
+  const R* bq = bg + DP;
+  const R* bc3 = bq + NQ;
+  const R* bc4 = bc3 + NC;
+  R s2[DP];  // st_v^2
+#pragma unroll
+  for (int v = 0; v < DP; ++v) s2[v] = st[v] * st[v];
+  R uv = beta[0], ub = R(0), us = R(0), uss = R(0), diag = R(0), sT = beta[0];
+  int iq = 0, ic = 0, i4 = 0;
+#pragma unroll
+  for (int i = 0; i < DP; ++i) {
+    R bv = bg[i], bb = R(0), bs = R(0), bss = R(0), bT = bg[i];
+#pragma unroll
+    for (int j = 0; j < DP; ++j) {
+      if (j < i) continue;
+      const R q = bq[iq++];
+      R av = q, ab = R(0), as = R(0), ass = R(0), aT = q;
+      if (i == j && i > 0) diag += R(2) * s2[i] * q;
+#pragma unroll
+      for (int k = 0; k < DP; ++k) {
+        if (k < j) continue;
+        const R t = bc3[ic++];
+        R ev = t, eb = R(0), es = R(0), eT = t;
+        if (i == j && j < k && i > 0) diag += R(2) * s2[i] * t * z[k];
+        if (i < j && j == k && j > 0) diag += R(2) * s2[j] * t * z[i];
+        if (i == j && j == k && i > 0) diag += R(6) * s2[i] * t * z[i];
+#pragma unroll
+        for (int l = 0; l < DP; ++l) {
+          if (l < k) continue;
+          const R f = bc4[i4++];
+          ev += f * z[l];
+          eb += f * bt[l];
+          if (l > 0) es += f * st[l];
+          eT += f * zT[l];
+          if (i == j && j == k && k == l) {
+            if (i > 0) diag += R(12) * s2[i] * f * z[i] * z[i];
+          } else if (i == j && j == k) {  // k < l
+            if (i > 0) diag += R(6) * s2[i] * f * z[i] * z[l];
+          } else if (j == k && k == l) {  // i < j
+            if (j > 0) diag += R(6) * s2[j] * f * z[i] * z[j];
+          } else if (i == j && k == l) {  // j < k
+            if (i > 0) diag += R(2) * s2[i] * f * z[k] * z[k];
+            if (k > 0) diag += R(2) * s2[k] * f * z[i] * z[i];
+          } else if (i == j) {  // j < k < l
+            if (i > 0) diag += R(2) * s2[i] * f * z[k] * z[l];
+          } else if (j == k) {  // i < j, k < l
+            if (j > 0) diag += R(2) * s2[j] * f * z[i] * z[l];
+          } else if (k == l) {  // i < j < k
+            if (k > 0) diag += R(2) * s2[k] * f * z[i] * z[j];
+          }
+        }
+        // (z_k, bt_k, st_k, 0) * (ev, eb, es, 0)
+        av += z[k] * ev;
+        ab += z[k] * eb + bt[k] * ev;
+        if (k > 0) {
+          as += z[k] * es + st[k] * ev;
+          ass += R(2) * st[k] * es;
+        } else {
+          as += z[k] * es;
+        }
+        aT += zT[k] * eT;
+        // keep the coefficient loads of one (i, j, k) group together
+        asm volatile("" ::: "memory");
+      }
+      // (z_j, bt_j, st_j, 0) * (av, ab, as, ass)
+      bv += z[j] * av;
+      bb += z[j] * ab + bt[j] * av;
+      if (j > 0) {
+        bs += z[j] * as + st[j] * av;
+        bss += z[j] * ass + R(2) * st[j] * as;
+      } else {
+        bs += z[j] * as;
+        bss += z[j] * ass;
+      }
+      bT += zT[j] * aT;
+    }
+    // (z_i, bt_i, st_i, 0) * (bv, bb, bs, bss)
+    uv += z[i] * bv;
+    ub += z[i] * bb + bt[i] * bv;
+    if (i > 0) {
+      us += z[i] * bs + st[i] * bv;
+      uss += z[i] * bss + R(2) * st[i] * bs;
+    } else {
+      us += z[i] * bs;
+      uss += z[i] * bss;
+    }
+    sT += zT[i] * bT;
+  }
+  uT = sT;
+  (void)us;
+  u = uv;
+  gen = ub + R(0.5) * ((R(1) - a.rho) * diag + a.rho * uss);
+}
+
 template <int VK, int EV, bool CC, typename R, int D>
 __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R, D> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -397,8 +508,9 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
           // with hit set always votes for itself, so its copies are never
           // skipped.  Without the vote the copies are 2 D predicated moves per
           // step; the vote and its branch pay off from d = 3 on, except next
-          // to the dense evaluation, whose registers leave no room for it.
-          constexpr bool VOTE = (EV == EV_TABLES) && D >= 3;
+          // to the degree-3 dense evaluation (up to d = 10), whose registers
+          // leave no room for it.
+          constexpr bool VOTE = (EV != EV_DENSE3) && D >= 3;
           const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
           if (any_hit) {
 #pragma unroll
@@ -454,7 +566,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const R tau = ti + ((R)sstar + theta) * h;
 
     R u = 0, gsum = 0, uT = 0;
-    if constexpr (EV == EV_DENSE3) {
+    if constexpr (EV == EV_DENSE3 || EV == EV_DENSE4) {
       R z[DP], zT[DP], bt[DP], st[DP];
       z[0] = (tau - a.ctr[0]) * a.sc[0];
       zT[0] = (a.T - a.ctr[0]) * a.sc[0];
@@ -467,7 +579,10 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
         bt[v] = drift_s[v - 1] * a.sc[v];
         st[v] = sig_s[v - 1] * a.sc[v];
       }
-      eval_dense3<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
+      if constexpr (EV == EV_DENSE4)
+        eval_dense4<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
+      else
+        eval_dense3<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
     } else {
       // per-thread Chebyshev tables: value, drift- and diffusion-scaled
       // derivatives at (tau, X_tau), value at (T, X_T)
@@ -644,7 +759,13 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
                  : (m.vol_kind == 3) ? VK_DUPIRE
                                      : VK_TANH;
   const unsigned grid = (unsigned)P.n * (unsigned)P.chunks;
-  if (dense) return launch_ev<EV_DENSE3, true>(vk, a, grid, tpb, smem, st);  // implies constant correlation
+  if (dense) {  // implies a constant correlation
+    if (P.dense4) {
+      if constexpr (D <= 5) return launch_ev<EV_DENSE4, true>(vk, a, grid, tpb, smem, st);
+      return cudaErrorInvalidValue;  // the host selects degree 4 only for d <= 5
+    }
+    return launch_ev<EV_DENSE3, true>(vk, a, grid, tpb, smem, st);
+  }
   if (cc) return launch_ev<EV_TABLES, true>(vk, a, grid, tpb, smem, st);
   return launch_ev<EV_TABLES, false>(vk, a, grid, tpb, smem, st);
 }

@@ -63,11 +63,22 @@ bool pack_multi_indices(const std::vector<std::vector<int>>& nus, std::vector<ui
   return true;
 }
 
-// Chebyshev -> monomial map of a basis of total degree <= 3.  Monomials in
-// the order constant, z_a, z_a z_b (a <= b), z_a z_b z_c (a <= b <= c), each
-// group lexicographic.  T_1 = z, T_2 = 2 z^2 - 1, T_3 = 4 z^3 - 3 z.
-int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, std::vector<int>& row,
-                       std::vector<int>& lidx, std::vector<double>& coef) {
+// Chebyshev -> monomial map of a basis of total degree <= 3 or 4.  Monomials
+// in the order constant, z_a, z_a z_b (a <= b), z_a z_b z_c (a <= b <= c)
+// and, for a degree-4 basis, z_a z_b z_c z_e (a <= b <= c <= e), each group
+// lexicographic.  T_1 = z, T_2 = 2 z^2 - 1, T_3 = 4 z^3 - 3 z,
+// T_4 = 8 z^4 - 8 z^2 + 1.
+int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, int max_deg,
+                       std::vector<int>& row, std::vector<int>& lidx, std::vector<double>& coef,
+                       int& mono_deg) {
+  int deg_max = 0;
+  for (const auto& nu : nus) {
+    int deg = 0;
+    for (int e : nu) deg += e;
+    if (deg > deg_max) deg_max = deg;
+  }
+  if (deg_max > max_deg || deg_max > 4) return -1;
+  mono_deg = deg_max > 3 ? 4 : 3;
   // index of each sorted multiset of variates
   std::vector<std::vector<int>> monos;
   monos.push_back({});
@@ -77,6 +88,11 @@ int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, std::ve
   for (int a = 0; a < dp; ++a)
     for (int b = a; b < dp; ++b)
       for (int c = b; c < dp; ++c) monos.push_back({a, b, c});
+  if (mono_deg == 4)
+    for (int a = 0; a < dp; ++a)
+      for (int b = a; b < dp; ++b)
+        for (int c = b; c < dp; ++c)
+          for (int e = c; e < dp; ++e) monos.push_back({a, b, c, e});
   const int pm = (int)monos.size();
   auto index_of = [&](const std::vector<int>& ms) {
     for (int m = 0; m < pm; ++m)
@@ -85,12 +101,12 @@ int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, std::ve
   };
   std::vector<std::vector<std::pair<int, double>>> rows(pm);
   // expansion of T_e as (power, coefficient)
-  const std::vector<std::pair<int, double>> cheb[4] = {
-      {{0, 1.0}}, {{1, 1.0}}, {{0, -1.0}, {2, 2.0}}, {{1, -3.0}, {3, 4.0}}};
+  const std::vector<std::pair<int, double>> cheb[5] = {{{0, 1.0}},
+                                                       {{1, 1.0}},
+                                                       {{0, -1.0}, {2, 2.0}},
+                                                       {{1, -3.0}, {3, 4.0}},
+                                                       {{0, 1.0}, {2, -8.0}, {4, 8.0}}};
   for (size_t l = 0; l < nus.size(); ++l) {
-    int deg = 0;
-    for (int e : nus[l]) deg += e;
-    if (deg > 3) return -1;
     // cartesian product over the variates
     std::vector<std::pair<std::vector<int>, double>> terms = {{std::vector<int>(dp, 0), 1.0}};
     for (int v = 0; v < dp; ++v) {

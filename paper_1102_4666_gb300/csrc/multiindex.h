@@ -15,7 +15,10 @@ bool pack_multi_indices(const std::vector<std::vector<int>>& nus, std::vector<ui
                         std::vector<uint8_t>& nnz, int& max_deg);
 
 // Chebyshev -> monomial map (CSR by monomial) of a basis of total degree
-// <= 3; returns the number of monomials C(dp + 3, 3), or -1 when a basis
-// function has a larger degree
-int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, std::vector<int>& row,
-                       std::vector<int>& lidx, std::vector<double>& coef);
+// deg <= max_deg (max_deg <= 4), deg the largest total degree in the basis;
+// the monomials are those of total degree <= max(deg, 3).  Returns their
+// number, C(dp + 3, 3) or C(dp + 4, 4), and sets mono_deg to 3 or 4; -1
+// when a basis function has a degree above max_deg
+int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, int max_deg,
+                       std::vector<int>& row, std::vector<int>& lidx, std::vector<double>& coef,
+                       int& mono_deg);

@@ -287,7 +287,8 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     }
     eta_used = mdeg;
     coeffs_valid = false;
-    pm = build_cheb_to_mono(nus, d + 1, conv_row, conv_l, conv_c);
+    // monomial (dense) evaluation: total degree <= 3, or <= 4 for d <= 5
+    pm = build_cheb_to_mono(nus, d + 1, d <= 5 ? 4 : 3, conv_row, conv_l, conv_c, mono_deg);
     if (pm < 0) pm = 0;
   }
   const int p = (int)nus.size();
@@ -309,7 +310,7 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   s.N = prm.N_steps;
   s.mixed = mixed;
   if (prm.eval_mode == 2 && pm == 0) {
-    err = "solve: eval_mode 2 (dense) needs a basis of total degree <= 3";
+    err = "solve: eval_mode 2 (dense) needs a basis of total degree <= 3 (<= 4 for d <= 5)";
     return BSDE_ERR_INVALID_ARG;
   }
   // the dense evaluation needs a constant correlation (all off-diagonal
@@ -323,6 +324,7 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     return BSDE_ERR_INVALID_ARG;
   }
   s.dense = pm > 0 && const_corr && prm.eval_mode != 1;
+  s.dense4 = s.dense && mono_deg == 4;
   if (prm.ls_mode != 0 && prm.ls_mode != 1) {
     err = "solve: ls_mode must be 0 (normal equations) or 1 (pivoted QR)";
     return BSDE_ERR_INVALID_ARG;
@@ -419,6 +421,7 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     P.out = (double*)take((OUT_SIZE + 1 + 2 * BSDE_DMAX) * 8);
     if (s.dense) {
       P.dense = true;
+      P.dense4 = s.dense4;
       P.pm = s.pm;
       P.beta = (double*)take((size_t)s.pm * 8);
       P.beta32 = (float*)take((size_t)s.pm * 4);

@@ -141,9 +141,15 @@ def _scale(cfg, nu, alpha, t, x):
     return max(1.0, phi_max, np.max(np.abs(u))) * (1.0 + cfg["lambda"] * cfg["T"])
 
 
-# (case, eval_mode): 0 automatic (dense monomial form for total degree <= 3
-# and constant correlation), 1 per-thread Chebyshev tables
-EVAL_CASES = [(n, 0) for n in CASES] + [(n, 1) for n in CASES if CASES[n][1]["eta"] <= 3]
+# (case, eval_mode): 0 automatic (dense monomial form for total degree <= 3,
+# or <= 4 at d <= 5, and a constant correlation), 1 per-thread Chebyshev
+# tables -- both forms wherever the dense one applies
+def _dense_applies(name):
+    cfg = _case(name)
+    return cfg["eta"] <= 3 or (cfg["eta"] == 4 and cfg["d"] <= 5)
+
+
+EVAL_CASES = [(n, 0) for n in CASES] + [(n, 1) for n in CASES if _dense_applies(n)]
 
 
 @pytest.mark.parametrize("name,ev", EVAL_CASES)
@@ -217,6 +223,25 @@ def test_full_size_c4_sampled_points(G, ev, shape):
     sc = _scale(cfg, nu, a0, t, x)
     assert np.max(np.abs(c[idx] - co)) < MIXED_C_TOL * sc
     # the refit at full size: normal equations of the GPU's own c
+    B = O.basis_matrix(cfg, nu, t, x)
+    assert rel(a1 - a0, O.fit(B, c)) < 1e-8
+
+
+def test_full_size_c3_sampled_points(G):
+    """c3 at its full size (d = 5, n = 2000, M = 5000, N = 50, total degree 4:
+    p = 210, per-thread Chebyshev tables), one mixed iteration; the oracle
+    recomputes c_i at a sample of points, and the refit solves the normal
+    equations of the GPU's own c."""
+    cfg = workloads.config("c3")
+    nu = O.multi_index_set(6, 4)
+    a0 = _alpha(cfg, nu, scale=1.0)
+    s = solver(G, cfg, "mixed")
+    t, x, c, a1 = s.iterate(3, a0)
+    s.close()
+    idx = np.arange(0, 2000, 250)
+    co = O.correction(cfg, nu, a0, 3, idx, t[idx], x[:, idx], nthreads=NTH)
+    sc = _scale(cfg, nu, a0, t, x)
+    assert np.max(np.abs(c[idx] - co)) < MIXED_C_TOL * sc
     B = O.basis_matrix(cfg, nu, t, x)
     assert rel(a1 - a0, O.fit(B, c)) < 1e-8
 
