@@ -173,8 +173,9 @@ typedef struct {
                                 BSDE_ERR_NOT_PD)                       */
   int eval_mode;    /* evaluation of u^k along the paths: 0 automatic, 1
                        per-thread Chebyshev tables (any degree), 2 dense
-                       monomial form (total degree <= 3, or <= 4 for
-                       d <= 5; constant correlation)                    */
+                       monomial form (constant correlation; total degree
+                       <= 3, or <= 4 for d <= 5; with BSDE_PREC_MIXED
+                       also <= 4 for d <= 10 and <= 6 for d <= 5)      */
   int paths_tpb;    /* threads per CTA of the path kernel (0: automatic;
                        32..256, a multiple of 32)                       */
   int paths_ppt;    /* paths per thread of the path kernel (0: automatic;

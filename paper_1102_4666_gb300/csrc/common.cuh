@@ -169,7 +169,8 @@ struct ProblemDev {
   // dense evaluation (basis of total degree <= 3, or <= 4 for d <= 5):
   // monomial coefficients
   bool dense = false;
-  bool dense4 = false;        // monomials up to degree 4
+  bool dense4 = false;        // monomials up to degree 4 (graded order)
+  int tree = 0;               // > 0: monomials up to this degree in prefix-tree order
   int pm = 0;                 // number of monomials, C(d + 4, 3) or C(d + 5, 4)
   double* beta = nullptr;     // [pm]
   float* beta32 = nullptr;    // [pm]

@@ -34,7 +34,10 @@ namespace paths {
 // volatility families: constant, a + phi(t) tanh(x - kappa) (sin/tanh),
 // Dupire's, and a + phi(t) |tanh(x - kappa)| (abs/tanh)
 enum { VK_CONST = 0, VK_TANH = 1, VK_DUPIRE = 2, VK_TANH_ABS = 3 };
-enum { EV_TABLES = 0, EV_DENSE3 = 1, EV_DENSE4 = 2 };
+// evaluation of u^k along the paths: per-thread Chebyshev tables, dense
+// monomial Horner loops for total degree <= 3 (any d) or 4 (d <= 5), or the
+// prefix-tree recursion for total degree EV (EV_TREE4..EV_TREE6)
+enum { EV_TABLES = 0, EV_DENSE3 = 1, EV_DENSE4 = 2, EV_TREE4 = 4, EV_TREE5 = 5, EV_TREE6 = 6 };
 
 // monomials of total degree <= 3 in dp variates: C(dp + 3, 3)
 __host__ __device__ constexpr int ncubic(int dp) { return (dp + 3) * (dp + 2) * (dp + 1) / 6; }
@@ -397,6 +400,95 @@ __device__ __forceinline__ void eval_dense4(const Args<R, D>& a, const R* __rest
   gen = ub + R(0.5) * ((R(1) - a.rho) * diag + a.rho * uss);
 }
 
+// ---------------------------------------------------------------------------
+// Dense evaluation of a basis of any total degree ETA by recursion over the
+// prefix tree of sorted variate multisets: node N (a multiset ending with
+// variate w) carries Q_N = beta_N + sum_{x >= w} z_x Q_{N+x}, so that u is
+// Q at the root.  Besides the value, its derivative along bt and its first
+// and second derivatives along st (as in the loops above), each node
+// returns
+//   DG_N = sum_v st_v^2 d2_vv Q_N = sum_x (z_x DG_{N+x} + 2 st_x^2 SD_{N+x}),
+//   SD_N = d_w Q_N = Q_{N+w} + z_w SD_{N+w},
+// the derivative of Q_N with respect to its own last variate (only the child
+// that repeats w depends on z_w).  The coefficients are stored in the
+// depth-first pre-order of the tree; every index is a compile-time constant.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct TreeAcc {
+  R v, b, s, ss, dg, sd, t;
+};
+
+// sorted multisets of size <= m over nvar variates: C(nvar + m, m)
+__host__ __device__ constexpr int tree_size(int nvar, int m) {
+  int r = 1;
+  for (int i = 1; i <= m; ++i) r = r * (nvar + i) / i;
+  return r;
+}
+
+template <typename R, int DP, int ETA, int DEPTH, int W, int IDX>
+__device__ __forceinline__ void tree_node(const R* __restrict__ beta, const R (&z)[DP],
+                                          const R (&zT)[DP], const R (&bt)[DP], const R (&st)[DP],
+                                          const R (&s2x2)[DP], TreeAcc<R>& a);
+
+// fold the children x = X .. DP-1 of a node at depth DEPTH (last variate W)
+template <typename R, int DP, int ETA, int DEPTH, int W, int X, int IDX>
+__device__ __forceinline__ void tree_children(const R* __restrict__ beta, const R (&z)[DP],
+                                              const R (&zT)[DP], const R (&bt)[DP],
+                                              const R (&st)[DP], const R (&s2x2)[DP],
+                                              TreeAcc<R>& a) {
+  if constexpr (X < DP) {
+    TreeAcc<R> c;
+    tree_node<R, DP, ETA, DEPTH + 1, X, IDX>(beta, z, zT, bt, st, s2x2, c);
+    a.v += z[X] * c.v;
+    a.b += z[X] * c.b + bt[X] * c.v;
+    if constexpr (X > 0) {
+      a.s += z[X] * c.s + st[X] * c.v;
+      a.ss += z[X] * c.ss + R(2) * st[X] * c.s;
+      a.dg += z[X] * c.dg + s2x2[X] * c.sd;
+    } else {  // the time variate has no diffusion
+      a.s += z[X] * c.s;
+      a.ss += z[X] * c.ss;
+      a.dg += z[X] * c.dg;
+    }
+    if constexpr (DEPTH > 0 && X == W) a.sd = c.v + z[X] * c.sd;
+    a.t += zT[X] * c.t;
+    tree_children<R, DP, ETA, DEPTH, W, X + 1, IDX + tree_size(DP - X, ETA - DEPTH - 1)>(
+        beta, z, zT, bt, st, s2x2, a);
+  }
+}
+
+template <typename R, int DP, int ETA, int DEPTH, int W, int IDX>
+__device__ __forceinline__ void tree_node(const R* __restrict__ beta, const R (&z)[DP],
+                                          const R (&zT)[DP], const R (&bt)[DP], const R (&st)[DP],
+                                          const R (&s2x2)[DP], TreeAcc<R>& a) {
+  const R c0 = beta[IDX];
+  a.v = c0;
+  a.t = c0;
+  a.b = a.s = a.ss = a.dg = a.sd = R(0);
+  if constexpr (DEPTH < ETA) {
+    tree_children<R, DP, ETA, DEPTH, W, (DEPTH == 0 ? 0 : W), IDX + 1>(beta, z, zT, bt, st, s2x2,
+                                                                      a);
+    // keep the coefficient loads of one group of leaves together
+    if constexpr (DEPTH == ETA - 1) asm volatile("" ::: "memory");
+  }
+}
+
+template <typename R, int D, int ETA>
+__device__ __forceinline__ void eval_tree(const Args<R, D>& a, const R* __restrict__ beta,
+                                          const R (&z)[D + 1], const R (&zT)[D + 1],
+                                          const R (&bt)[D + 1], const R (&st)[D + 1], R& u,
+                                          R& gen, R& uT) {
+  constexpr int DP = D + 1;
+  R s2x2[DP];
+#pragma unroll
+  for (int v = 0; v < DP; ++v) s2x2[v] = R(2) * st[v] * st[v];
+  TreeAcc<R> r;
+  tree_node<R, DP, ETA, 0, 0, 0>(beta, z, zT, bt, st, s2x2, r);
+  u = r.v;
+  uT = r.t;
+  gen = r.b + R(0.5) * ((R(1) - a.rho) * r.dg + a.rho * r.ss);
+}
+
 template <int VK, int EV, bool CC, typename R, int D>
 __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R, D> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -508,9 +600,9 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
           // with hit set always votes for itself, so its copies are never
           // skipped.  Without the vote the copies are 2 D predicated moves per
           // step; the vote and its branch pay off from d = 3 on, except next
-          // to the degree-3 dense evaluation (up to d = 10), whose registers
-          // leave no room for it.
-          constexpr bool VOTE = (EV != EV_DENSE3) && D >= 3;
+          // to the dense evaluations of d >= 6 (the degree-3 loops at any d),
+          // whose registers leave no room for it.
+          constexpr bool VOTE = D >= 3 && EV != EV_DENSE3 && !(EV >= EV_TREE4 && D >= 6);
           const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
           if (any_hit) {
 #pragma unroll
@@ -566,7 +658,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const R tau = ti + ((R)sstar + theta) * h;
 
     R u = 0, gsum = 0, uT = 0;
-    if constexpr (EV == EV_DENSE3 || EV == EV_DENSE4) {
+    if constexpr (EV != EV_TABLES) {
       R z[DP], zT[DP], bt[DP], st[DP];
       z[0] = (tau - a.ctr[0]) * a.sc[0];
       zT[0] = (a.T - a.ctr[0]) * a.sc[0];
@@ -579,7 +671,9 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
         bt[v] = drift_s[v - 1] * a.sc[v];
         st[v] = sig_s[v - 1] * a.sc[v];
       }
-      if constexpr (EV == EV_DENSE4)
+      if constexpr (EV >= EV_TREE4)
+        eval_tree<R, D, EV>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
+      else if constexpr (EV == EV_DENSE4)
         eval_dense4<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
       else
         eval_dense3<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
@@ -684,6 +778,29 @@ cudaError_t launch_ev(int vk, const Args<R, D>& a, unsigned grid, int tpb, size_
   }
 }
 
+// the prefix-tree evaluations (FP32 paths only: FP64 solves of these bases
+// use the tables), compiled in translation units of their own
+template <typename R, int D>
+cudaError_t launch_tree(int eta, int vk, const Args<R, D>& a, unsigned grid, int tpb, size_t smem,
+                        cudaStream_t st) {
+  switch (eta) {
+    case 4:
+      if constexpr (D >= 6 && sizeof(R) == 4)
+        return launch_ev<EV_TREE4, true>(vk, a, grid, tpb, smem, st);
+      return cudaErrorInvalidValue;
+    case 5:
+      if constexpr (D <= 5 && sizeof(R) == 4)
+        return launch_ev<EV_TREE5, true>(vk, a, grid, tpb, smem, st);
+      return cudaErrorInvalidValue;
+    case 6:
+      if constexpr (D <= 5 && sizeof(R) == 4)
+        return launch_ev<EV_TREE6, true>(vk, a, grid, tpb, smem, st);
+      return cudaErrorInvalidValue;
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 template <typename R, int D>
 cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, int M, int N,
                    uint32_t k, int tpb, int ppt, cudaStream_t st) {
@@ -760,11 +877,18 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
                                      : VK_TANH;
   const unsigned grid = (unsigned)P.n * (unsigned)P.chunks;
   if (dense) {  // implies a constant correlation
-    if (P.dense4) {
-      if constexpr (D <= 5) return launch_ev<EV_DENSE4, true>(vk, a, grid, tpb, smem, st);
-      return cudaErrorInvalidValue;  // the host selects degree 4 only for d <= 5
+    // the host selects: degree <= 3 loops (any d), degree-4 loops (d <= 5),
+    // the tree recursion of degree 4 (d >= 6) or 5 and 6 (d <= 5)
+    switch (P.tree) {
+      case 0:
+        if (P.dense4) {
+          if constexpr (D <= 5) return launch_ev<EV_DENSE4, true>(vk, a, grid, tpb, smem, st);
+          return cudaErrorInvalidValue;
+        }
+        return launch_ev<EV_DENSE3, true>(vk, a, grid, tpb, smem, st);
+      default:
+        return launch_tree<R, D>(P.tree, vk, a, grid, tpb, smem, st);
     }
-    return launch_ev<EV_DENSE3, true>(vk, a, grid, tpb, smem, st);
   }
   if (cc) return launch_ev<EV_TABLES, true>(vk, a, grid, tpb, smem, st);
   return launch_ev<EV_TABLES, false>(vk, a, grid, tpb, smem, st);
@@ -772,10 +896,19 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
 
 }  // namespace paths
 
-// one translation unit per (d, precision), so that the build compiles them in parallel
+// one translation unit per (d, precision), so that the build compiles them
+// in parallel; the FP32 prefix-tree kernels in one more per d
 #define BSDE_PATHS_INSTANTIATE(DV, R, SUF)                                                    \
+  extern template cudaError_t paths::launch_tree<R, DV>(int, int, const paths::Args<R, DV>&, \
+                                                        unsigned, int, size_t, cudaStream_t); \
   cudaError_t launch_paths_d##DV##_##SUF(const ModelHost& m, const GridHost& g,               \
                                          const ProblemDev& P, int M, int N, uint32_t k,       \
                                          int tpb, int ppt, cudaStream_t st) {                 \
     return paths::launch<R, DV>(m, g, P, M, N, k, tpb, ppt, st);                              \
   }
+
+#define BSDE_PATHS_INSTANTIATE_TREE(DV)                                                     \
+  template cudaError_t paths::launch_tree<float, DV>(int, int, const paths::Args<float, DV>&, \
+                                                     unsigned, int, size_t, cudaStream_t);    \
+  template cudaError_t paths::launch_tree<double, DV>(int, int, const paths::Args<double, DV>&, \
+                                                      unsigned, int, size_t, cudaStream_t);

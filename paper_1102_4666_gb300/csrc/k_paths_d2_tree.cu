@@ -1,0 +1,4 @@
+// k_paths_d2_tree.cu -- prefix-tree (dense, degree 4..6) evaluation kernels of the path kernel
+// for d = 2 assets.
+#include "k_paths.cuh"
+BSDE_PATHS_INSTANTIATE_TREE(2)

@@ -4,6 +4,8 @@
 // ascending, then lexicographically descending with the time variate first.
 #include "multiindex.h"
 
+#include <map>
+
 #include <cmath>
 
 namespace {
@@ -128,6 +130,86 @@ int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, int max
       const int m = index_of(ms);
       if (m < 0) return -1;
       rows[m].push_back({(int)l, t.second});
+    }
+  }
+  row.assign(pm + 1, 0);
+  lidx.clear();
+  coef.clear();
+  for (int m = 0; m < pm; ++m) {
+    for (const auto& e : rows[m]) {
+      lidx.push_back(e.first);
+      coef.push_back(e.second);
+    }
+    row[m + 1] = (int)lidx.size();
+  }
+  return pm;
+}
+
+namespace {
+// monomials of total degree <= deg as sorted variate lists, depth-first
+void tree_monos(int dp, int deg, std::vector<int>& prefix, std::vector<std::vector<int>>& out) {
+  out.push_back(prefix);
+  if ((int)prefix.size() == deg) return;
+  const int w = prefix.empty() ? 0 : prefix.back();
+  for (int x = w; x < dp; ++x) {
+    prefix.push_back(x);
+    tree_monos(dp, deg, prefix, out);
+    prefix.pop_back();
+  }
+}
+}  // namespace
+
+int build_cheb_to_mono_tree(const std::vector<std::vector<int>>& nus, int dp,
+                            std::vector<int>& row, std::vector<int>& lidx,
+                            std::vector<double>& coef, int& mono_deg) {
+  int deg_max = 0;
+  for (const auto& nu : nus) {
+    int deg = 0;
+    for (int e : nu) deg += e;
+    if (deg > deg_max) deg_max = deg;
+  }
+  if (deg_max > 6) return -1;
+  mono_deg = deg_max;
+  std::vector<std::vector<int>> monos;
+  std::vector<int> prefix;
+  tree_monos(dp, deg_max, prefix, monos);
+  const int pm = (int)monos.size();
+  std::map<std::vector<int>, int> index;
+  for (int m = 0; m < pm; ++m) index[monos[m]] = m;
+  // T_e as (power, coefficient), from T_{e+1} = 2 z T_e - T_{e-1}
+  std::vector<std::vector<double>> T(7);
+  T[0] = {1.0};
+  T[1] = {0.0, 1.0};
+  for (int e = 1; e < 6; ++e) {
+    std::vector<double> nxt(e + 2, 0.0);
+    for (int q = 0; q <= e; ++q) nxt[q + 1] += 2.0 * T[e][q];
+    for (int q = 0; q < (int)T[e - 1].size(); ++q) nxt[q] -= T[e - 1][q];
+    T[e + 1] = nxt;
+  }
+  std::vector<std::vector<std::pair<int, double>>> rows(pm);
+  for (size_t l = 0; l < nus.size(); ++l) {
+    // cartesian product over the active variates of the powers of T_e
+    std::vector<std::pair<std::vector<int>, double>> terms = {{std::vector<int>(dp, 0), 1.0}};
+    for (int v = 0; v < dp; ++v) {
+      const int e = nus[l][v];
+      if (e == 0) continue;
+      std::vector<std::pair<std::vector<int>, double>> next;
+      for (const auto& t : terms)
+        for (int q = 0; q <= e; ++q) {
+          if (T[e][q] == 0.0) continue;
+          auto mu = t.first;
+          mu[v] = q;
+          next.push_back({mu, t.second * T[e][q]});
+        }
+      terms.swap(next);
+    }
+    for (const auto& t : terms) {
+      std::vector<int> ms;
+      for (int v = 0; v < dp; ++v)
+        for (int q = 0; q < t.first[v]; ++q) ms.push_back(v);
+      const auto it = index.find(ms);
+      if (it == index.end()) return -1;
+      rows[it->second].push_back({(int)l, t.second});
     }
   }
   row.assign(pm + 1, 0);

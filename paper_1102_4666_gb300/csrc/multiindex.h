@@ -22,3 +22,14 @@ bool pack_multi_indices(const std::vector<std::vector<int>>& nus, std::vector<ui
 int build_cheb_to_mono(const std::vector<std::vector<int>>& nus, int dp, int max_deg,
                        std::vector<int>& row, std::vector<int>& lidx, std::vector<double>& coef,
                        int& mono_deg);
+
+// The same map for a basis of total degree deg <= 6 onto all monomials of
+// total degree <= deg, in the depth-first pre-order of the prefix tree of
+// sorted variate multisets (root = constant; the children of a multiset
+// ending with variate w append a variate x >= w): the order in which the
+// generic dense evaluation of the path kernel visits them.  Returns the
+// number of monomials C(dp + deg, deg) and sets mono_deg = deg; -1 when deg
+// is above 6.
+int build_cheb_to_mono_tree(const std::vector<std::vector<int>>& nus, int dp,
+                            std::vector<int>& row, std::vector<int>& lidx,
+                            std::vector<double>& coef, int& mono_deg);

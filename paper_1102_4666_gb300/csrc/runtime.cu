@@ -287,8 +287,25 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     }
     eta_used = mdeg;
     coeffs_valid = false;
-    // monomial (dense) evaluation: total degree <= 3, or <= 4 for d <= 5
-    pm = build_cheb_to_mono(nus, d + 1, d <= 5 ? 4 : 3, conv_row, conv_l, conv_c, mono_deg);
+    // monomial (dense) evaluation: Horner loops for total degree <= 3 (any
+    // d) or 4 (d <= 5); with FP32 paths, the prefix-tree recursion for
+    // degree 4 (d <= 10) and degrees 5 and 6 (d <= 5); beyond that the
+    // per-thread Chebyshev tables
+    int deg_max = 0;
+    for (const auto& nu : nus) {
+      int deg = 0;
+      for (int e : nu) deg += e;
+      deg_max = deg > deg_max ? deg : deg_max;
+    }
+    tree_deg = 0;
+    if (deg_max <= 3 || (deg_max == 4 && d <= 5)) {
+      pm = build_cheb_to_mono(nus, d + 1, 4, conv_row, conv_l, conv_c, mono_deg);
+    } else if (mixed && ((deg_max == 4 && d <= 10) || (deg_max <= 6 && d <= 5))) {
+      pm = build_cheb_to_mono_tree(nus, d + 1, conv_row, conv_l, conv_c, mono_deg);
+      tree_deg = pm > 0 ? mono_deg : 0;
+    } else {
+      pm = -1;
+    }
     if (pm < 0) pm = 0;
   }
   const int p = (int)nus.size();
@@ -310,7 +327,8 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   s.N = prm.N_steps;
   s.mixed = mixed;
   if (prm.eval_mode == 2 && pm == 0) {
-    err = "solve: eval_mode 2 (dense) needs a basis of total degree <= 3 (<= 4 for d <= 5)";
+    err = "solve: eval_mode 2 (dense) needs a basis of total degree <= 3, <= 4 (d <= 5; with "
+          "FP32 paths d <= 10) or, with FP32 paths, <= 6 (d <= 5)";
     return BSDE_ERR_INVALID_ARG;
   }
   // the dense evaluation needs a constant correlation (all off-diagonal
@@ -324,7 +342,8 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     return BSDE_ERR_INVALID_ARG;
   }
   s.dense = pm > 0 && const_corr && prm.eval_mode != 1;
-  s.dense4 = s.dense && mono_deg == 4;
+  s.dense4 = s.dense && tree_deg == 0 && mono_deg == 4;
+  s.tree = s.dense ? tree_deg : 0;
   if (prm.ls_mode != 0 && prm.ls_mode != 1) {
     err = "solve: ls_mode must be 0 (normal equations) or 1 (pivoted QR)";
     return BSDE_ERR_INVALID_ARG;
@@ -422,6 +441,7 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     if (s.dense) {
       P.dense = true;
       P.dense4 = s.dense4;
+      P.tree = s.tree;
       P.pm = s.pm;
       P.beta = (double*)take((size_t)s.pm * 8);
       P.beta32 = (float*)take((size_t)s.pm * 4);

@@ -21,12 +21,12 @@ struct Allocator {
 
 struct Shape {
   int d = 0, n = 0, n_pad = 0, p = 0, p_pad = 0, eta = 0, M = 0, N = 0;
-  int chunks = 0, tpb = 0, ppt = 0, splits = 0, pm = 0;
+  int chunks = 0, tpb = 0, ppt = 0, splits = 0, pm = 0, tree = 0;
   bool mixed = false, dense = false, dense4 = false, qr = false;
   bool operator==(const Shape& o) const {
     return d == o.d && n == o.n && p == o.p && eta == o.eta && M == o.M && N == o.N &&
            tpb == o.tpb && ppt == o.ppt && mixed == o.mixed && dense == o.dense &&
-           dense4 == o.dense4 && pm == o.pm && qr == o.qr;
+           dense4 == o.dense4 && tree == o.tree && pm == o.pm && qr == o.qr;
   }
 };
 
@@ -42,9 +42,9 @@ class Problem {
   std::vector<uint8_t> nnz;
   std::vector<std::vector<int>> nus;
   int eta_used = 0;  // largest single-variate degree present
-  // Chebyshev -> monomial map when the total degree is <= 3, or <= 4 for
-  // d <= 5 (pm > 0; mono_deg: the largest monomial degree, 3 or 4)
-  int pm = 0, mono_deg = 3;
+  // Chebyshev -> monomial map of the dense evaluation (pm > 0; mono_deg:
+  // the largest monomial degree; tree_deg > 0: prefix-tree order)
+  int pm = 0, mono_deg = 3, tree_deg = 0;
   std::vector<int> conv_row, conv_l;
   std::vector<double> conv_c;
   std::string err;

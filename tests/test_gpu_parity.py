@@ -108,6 +108,10 @@ CASES = {
     # count (the last group of two steps is half full) and a few paths
     "d10_one_step_one_path": ("c4", dict(n=160, M=1, N=1, eta=2)),
     "d5_odd_steps": ("c3", dict(n=60, M=5, N=3, eta=2)),
+    # dense evaluation by the prefix-tree recursion: degree 4 at d = 10
+    # (p = 1365) and degree 5 at d = 5 (p = 462)
+    "d10_degree4": ("c4", dict(n=2800, M=16, N=5, eta=4)),
+    "d5_degree5": ("c3", dict(n=940, M=40, N=6, eta=5)),
 }
 
 
@@ -142,11 +146,11 @@ def _scale(cfg, nu, alpha, t, x):
 
 
 # (case, eval_mode): 0 automatic (dense monomial form for total degree <= 3,
-# or <= 4 at d <= 5, and a constant correlation), 1 per-thread Chebyshev
-# tables -- both forms wherever the dense one applies
+# <= 4 at d <= 10 or <= 6 at d <= 5, and a constant correlation), 1
+# per-thread Chebyshev tables -- both forms wherever the dense one applies
 def _dense_applies(name):
     cfg = _case(name)
-    return cfg["eta"] <= 3 or (cfg["eta"] == 4 and cfg["d"] <= 5)
+    return cfg["eta"] <= 3 or (cfg["eta"] == 4 and cfg["d"] <= 10) or (cfg["eta"] <= 6 and cfg["d"] <= 5)
 
 
 EVAL_CASES = [(n, 0) for n in CASES] + [(n, 1) for n in CASES if _dense_applies(n)]
