@@ -195,15 +195,21 @@ def run_reference(args):
 def run_profile_case(args):
     """A small launch of the same kernels for ncu: the d = 10 workload with
     n = 800 points and one iteration (every kernel of an iteration runs
-    once per solve)."""
+    once per solve); `--case profile_tree`: the same model with a degree-4
+    basis (p = 1365, prefix-tree evaluation), n = 2800, M = 2000, N = 50."""
     import torch
     import paper_1102_4666_gb300 as G
-    cfg = workloads.config(CONFIG, n=800, K_it=1)
+    if args.case == "profile_tree":
+        cfg = workloads.config(CONFIG, n=2800, M=2000, N=50, eta=4, K_it=1)
+        label = " eta=4 n=2800 M=2000 N=50 K_it=1"
+    else:
+        cfg = workloads.config(CONFIG, n=800, K_it=1)
+        label = " n=800 K_it=1"
     s = G.Solver(cfg, precision=args.precision)
     for _ in range(2):
         r = s.solve(use_graph=0, timing=1)
     torch.cuda.synchronize()
-    print(json.dumps({"case": "profile", "workload": cfg["name"] + " n=800 K_it=1",
+    print(json.dumps({"case": args.case, "workload": cfg["name"] + label,
                       "precision": args.precision, "ms_paths": r.ms_paths, "ms_gram": r.ms_gram,
                       "ms_solve": r.ms_solve, "ms_total": r.ms_total, "price": r.price}))
     s.close()
@@ -483,12 +489,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--case", default="bench", choices=["bench", "profile", "profile_tree"])
     ap.add_argument("--serving-requests", type=int, default=100,
                     help="requests of the Poisson serving mix (0: skip; 2000: the full mix)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     args = ap.parse_args()
-    if args.case == "profile":
+    if args.case in ("profile", "profile_tree"):
         return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)

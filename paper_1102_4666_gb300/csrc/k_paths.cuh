@@ -563,9 +563,19 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
   const int ppc = tpb * a.ppt;
   double acc = 0.0;
 
+  // The prefix-tree evaluation is tens of kilobytes of straight-line code
+  // run once per path: the warps of a CTA enter it together (a barrier
+  // before it), so that one warp's instruction fetches serve the others.
+  // The loop then runs the same number of paths on every thread of the CTA;
+  // threads past the last path compute one that is discarded.
+  constexpr bool SYNC_EVAL = EV >= EV_TREE4;
   for (int jp = 0; jp < a.ppt; ++jp) {
     const int m = chunk * ppc + jp * tpb + tid;
-    if (m >= a.M) break;
+    if constexpr (SYNC_EVAL) {
+      if (chunk * ppc + jp * tpb >= a.M) break;  // no path left in the CTA
+    } else {
+      if (m >= a.M) break;
+    }
     // the uniform random time: U = (s* + theta) / N from one 32-bit word
     const uint4 ou = philox_rk(a, 0u, (uint32_t)m, (uint32_t)i, tagU);
     const uint64_t wN = (uint64_t)ou.x * (uint64_t)a.N;
@@ -656,6 +666,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
       Xtau[j] = Xs[j] + theta * (Xn[j] - Xs[j]) + sig_s[j] * bb * y;
     }
     const R tau = ti + ((R)sstar + theta) * h;
+    if constexpr (SYNC_EVAL) __syncthreads();
 
     R u = 0, gsum = 0, uT = 0;
     if constexpr (EV != EV_TABLES) {
@@ -725,7 +736,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const R f = -a.r * u + a.lam * Math<R>::fmax(obs - u, R(0));
     const R phiT = basket_value<R, D>(a, X, true);
     const R am = (a.T - ti) * (f + gsum) + phiT - uT;
-    acc += (double)am;
+    if (!SYNC_EVAL || m < a.M) acc += (double)am;
   }
 
   // fixed-order CTA reduction of the per-thread sums
