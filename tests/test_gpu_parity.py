@@ -112,6 +112,11 @@ CASES = {
     # (p = 1365) and degree 5 at d = 5 (p = 462)
     "d10_degree4": ("c4", dict(n=2800, M=16, N=5, eta=4)),
     "d5_degree5": ("c3", dict(n=940, M=40, N=6, eta=5)),
+    # a full correlation matrix (no constant correlation): the general
+    # triangular product L Z in the Euler step and the correlation-weighted
+    # cross terms of the per-thread table evaluation
+    "d3_full_corr": ("c3", dict(d=3, n=90, M=130, N=9, eta=3,
+                                corr=[[1.0, 0.3, -0.1], [0.3, 1.0, 0.5], [-0.1, 0.5, 1.0]])),
 }
 
 
@@ -150,6 +155,8 @@ def _scale(cfg, nu, alpha, t, x):
 # per-thread Chebyshev tables -- both forms wherever the dense one applies
 def _dense_applies(name):
     cfg = _case(name)
+    if cfg.get("corr") is not None:
+        return False
     return cfg["eta"] <= 3 or (cfg["eta"] == 4 and cfg["d"] <= 10) or (cfg["eta"] <= 6 and cfg["d"] <= 5)
 
 
@@ -368,3 +375,16 @@ def test_errors_are_status_codes(G):
     s3 = solver(G, bad, "fp64")
     assert s3.solve(check=False).status == G.ERR_INVALID_ARG
     s3.close()
+    # the dense evaluation forced where it does not apply: a full correlation
+    # matrix, and a degree-5 basis with FP64 paths (tree kernels are FP32)
+    full = _case("d3_full_corr")
+    full["K_it"] = 1
+    s4 = solver(G, full, "mixed")
+    assert s4.solve(check=False, eval_mode=2).status == G.ERR_INVALID_ARG
+    assert s4.solve(check=False, eval_mode=0).status == G.OK
+    s4.close()
+    deg5 = workloads.config("c3", n=940, M=16, N=3, eta=5, K_it=1)
+    s5 = solver(G, deg5, "fp64")
+    assert s5.solve(check=False, eval_mode=2).status == G.ERR_INVALID_ARG
+    assert s5.solve(check=False, eval_mode=0).status == G.OK
+    s5.close()
