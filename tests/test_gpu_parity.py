@@ -238,6 +238,23 @@ def test_full_size_c4_sampled_points(G, ev, shape):
     assert rel(a1 - a0, O.fit(B, c)) < 1e-8
 
 
+def test_full_size_c4_sampled_points_fp64(G):
+    """The plain FP64 path at the full d = 10 size: one iteration; the oracle
+    recomputes c_i at a sample of points to 1e-9 of the integrand's scale."""
+    cfg = workloads.config("c4")
+    nu = O.multi_index_set(11, 3)
+    a0 = _alpha(cfg, nu, scale=1.0)
+    s = solver(G, cfg, "fp64")
+    t, x, c, a1 = s.iterate(5, a0)
+    s.close()
+    idx = np.arange(0, 4000, 500)
+    co = O.correction(cfg, nu, a0, 5, idx, t[idx], x[:, idx], nthreads=NTH)
+    sc = _scale(cfg, nu, a0, t, x)
+    assert np.max(np.abs(c[idx] - co)) < 1e-9 * sc
+    B = O.basis_matrix(cfg, nu, t, x)
+    assert rel(a1 - a0, O.fit(B, c)) < 1e-9
+
+
 def test_full_size_c3_sampled_points(G):
     """c3 at its full size (d = 5, n = 2000, M = 5000, N = 50, total degree 4:
     p = 210, per-thread Chebyshev tables), one mixed iteration; the oracle
