@@ -306,6 +306,25 @@ def fp64_sequential_model(reqs, arrivals):
             "path_steps_per_s": total / (t_free - 0.0)}
 
 
+def run_serving_fp64_measured(n_requests=24, seed=17, load=0.7, m_div=8):
+    """The plain comparator measured rather than modeled: a smaller mix (the
+    serving mix with M divided by m_div) at an arrival rate the FP64
+    one-request-at-a-time server sustains (`load` times its measured
+    capacity), served by it and, on the same arrivals, by the mixed-precision
+    continuous-batching server (4 slots, FIFO)."""
+    reqs = workloads.serving_mix(n_requests, seed=seed)
+    for r in reqs:
+        r["M"] = max(200, r["M"] // m_div)
+    mean_steps = sum(workloads.path_steps(r) for r in reqs) / len(reqs)
+    cap64 = serving_capacity(reqs[:6], slots=1, precision="fp64")
+    rate = load * cap64 / mean_steps
+    arr = arrival_times(len(reqs), rate, seed)
+    return {"requests": len(reqs), "M_divided_by": m_div, "arrival_rate_hz": rate,
+            "fp64_capacity_path_steps_per_s": cap64, "load_of_fp64": load,
+            "fp64_one_at_a_time": run_serving(reqs, arr, precision="fp64", slots=1, policy="fifo"),
+            "mixed_4_slots": run_serving(reqs, arr, precision="mixed", slots=4, policy="fifo")}
+
+
 def run_serving_suite(n_requests, seed=7, load=0.8):
     """One seeded request mix and one arrival stream (rate: `load` times the
     16-slot capacity), served by the continuous-batching server with 16 or 4
@@ -325,6 +344,7 @@ def run_serving_suite(n_requests, seed=7, load=0.8):
     out["response_ratio_4"] = run_serving(reqs, arr, slots=4, policy="response_ratio")
     out["one_at_a_time_mixed"] = run_serving(reqs, arr, slots=1, policy="fifo")
     out["one_at_a_time_fp64"] = fp64_sequential_model(reqs, arr)
+    out["fp64_comparator_measured"] = run_serving_fp64_measured()
     return out
 
 
