@@ -21,30 +21,52 @@ __global__ void k_reduce_c(int n, int chunks, int M, const double* __restrict__ 
   c[i] = s / (double)M;
 }
 
-// warp per basis function: out[l] = sum_i B[l][i] y[i] (fixed lane order
-// and shuffle tree); with sub != nullptr, out[l] = sub[l] - that sum
-__global__ void k_bt_times(int n, int n_pad, int p, const double* __restrict__ B,
-                           const double* __restrict__ y, const double* __restrict__ sub,
-                           double* __restrict__ out) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= p) return;
-  const double* row = B + (size_t)warp * n_pad;
+// CTA of 128 threads per basis function: out[l] = sum_i B[l][i] y[i], each
+// thread over i = tid mod 128, then a fixed shuffle tree and the four warp
+// sums in order; with sub != nullptr, out[l] = sub[l] - that sum
+__global__ void __launch_bounds__(128) k_bt_times(int n, int n_pad, int p,
+                                                  const double* __restrict__ B,
+                                                  const double* __restrict__ y,
+                                                  const double* __restrict__ sub,
+                                                  double* __restrict__ out) {
+  __shared__ double ws[4];
+  const int l = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double* row = B + (size_t)l * n_pad;
   double s = 0.0;
-  for (int i = lane; i < n; i += 32) s += row[i] * y[i];
+  for (int i = tid; i < n; i += 128) s += row[i] * y[i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[warp] = sub ? (sub[warp] - s) : s;
+  if (lane == 0) ws[warp] = s;
+  __syncthreads();
+  if (tid == 0) {
+    const double tot = (ws[0] + ws[1]) + (ws[2] + ws[3]);
+    out[l] = sub ? (sub[l] - tot) : tot;
+  }
 }
 
-// thread per point: v[i] = sum_l B[l][i] x[l]
-__global__ void k_b_times(int n, int n_pad, int p, const double* __restrict__ B,
-                          const double* __restrict__ x, double* __restrict__ v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// v[i] = sum_l B[l][i] x[l]: CTA of 32 points x 8 slices of the basis
+// functions (coalesced rows of B per warp), the slice sums added in order
+__global__ void __launch_bounds__(256) k_b_times(int n, int n_pad, int p,
+                                                 const double* __restrict__ B,
+                                                 const double* __restrict__ x,
+                                                 double* __restrict__ v) {
+  __shared__ double part[8][33];
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const int per = (p + 7) / 8;
+  const int l0 = slice * per, l1 = min(p, l0 + per);
   double s = 0.0;
-  for (int l = 0; l < p; ++l) s += B[(size_t)l * n_pad + i] * x[l];
-  v[i] = s;
+  if (i < n)
+    for (int l = l0; l < l1; ++l) s += B[(size_t)l * n_pad + i] * x[l];
+  part[slice][lane] = s;
+  __syncthreads();
+  if (slice == 0 && i < n) {
+    double tot = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tot += part[q][lane];
+    v[i] = tot;
+  }
 }
 
 // FP64 Gram A = B B^T on CUDA cores: one 32x32 upper tile per CTA, written
@@ -246,7 +268,8 @@ __global__ void __launch_bounds__(256) k_chol_solve(const double* __restrict__ A
   for (int r = tid; r < p; r += blockDim.x) yv[r] = b ? b[r] : (r == (int)blockIdx.x ? 1.0 : 0.0);
   __syncthreads();
   const int nblk = (p + 31) / 32;
-  for (int blk = 0; blk < nblk; ++blk) {
+  // for b = e_j the forward solution is zero above row j: start at its block
+  for (int blk = b ? 0 : (int)blockIdx.x / 32; blk < nblk; ++blk) {
     const int c0 = blk * 32, nb = min(32, p - c0);
     if (warp == 0) {
       double yi = lane < nb ? yv[c0 + lane] : 0.0;
@@ -454,7 +477,7 @@ void launch_gram_f64(const ProblemDev& P, cudaStream_t st) {
 }
 
 void launch_rhs(const ProblemDev& P, cudaStream_t st) {
-  k_bt_times<<<(P.p * 32 + 255) / 256, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.c, nullptr, P.rhs);
+  k_bt_times<<<P.p, 128, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.c, nullptr, P.rhs);
 }
 
 void launch_cholesky(const ProblemDev& P, int nb, cudaStream_t st) {
@@ -471,8 +494,8 @@ void launch_cholesky(const ProblemDev& P, int nb, cudaStream_t st) {
 }
 
 void launch_refine_residual(const ProblemDev& P, cudaStream_t st) {
-  k_b_times<<<(P.n + 255) / 256, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.delta, P.v);
-  k_bt_times<<<(P.p * 32 + 255) / 256, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.v, P.rhs, P.res);
+  k_b_times<<<(P.n + 31) / 32, 256, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.delta, P.v);
+  k_bt_times<<<P.p, 128, 0, st>>>(P.n, P.n_pad, P.p, P.B, P.v, P.rhs, P.res);
 }
 
 void launch_update(const ProblemDev& P, int k, cudaStream_t st) {

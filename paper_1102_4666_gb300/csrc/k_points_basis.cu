@@ -43,16 +43,39 @@ __device__ __forceinline__ float to_tf32(float v) {
 
 // B[l][i] = prod over the active variates v of T_{nu_lv}(xi_v(t_i, x_i)),
 // xi_v = (2 y_v - (lo_v + hi_v)) / (hi_v - lo_v), Chebyshev T_e by the
-// three-term recurrence.  With split != 0 also writes the 3xTF32 operands
-// of the tensor-core Gram: hi = tf32(fp32(B)), lo = tf32(fp32(B) - hi).
-__global__ void k_basis(int n, int n_pad, int p, const uint2* __restrict__ pairs,
+// three-term recurrence.  Each thread first tabulates T_0..T_eta of its
+// point's dp reduced coordinates in shared memory ([v][e][thread], read back
+// only by the same thread), so that the FP64 division and recurrence run
+// once per (point, variate) instead of once per (point, basis function,
+// active variate); the products are then formed in the same order as the
+// definition.  With split != 0 also writes the 3xTF32 operands of the
+// tensor-core Gram: hi = tf32(fp32(B)), lo = tf32(fp32(B) - hi).
+__global__ void k_basis(int n, int n_pad, int p, int dp, int eta, const uint2* __restrict__ pairs,
                         const uint8_t* __restrict__ nnz, const double* __restrict__ t,
                         const double* __restrict__ x, const __grid_constant__ BoxArgs box,
                         double* __restrict__ B, float* __restrict__ Bhi,
                         float* __restrict__ Blo, int split) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int l0 = blockIdx.y * 32;
+  extern __shared__ double cheb[];
+  const int tid = threadIdx.x, tpb = blockDim.x;
+  const int i = blockIdx.x * tpb + tid;
   if (i >= n) return;
+  const int ne = eta + 1;
+  for (int v = 0; v < dp; ++v) {
+    const double y = (v == 0) ? t[i] : x[(size_t)(v - 1) * n + i];
+    const double xi = __ddiv_rn(__dsub_rn(__dmul_rn(2.0, y), __dadd_rn(box.lo[v], box.hi[v])),
+                                __dsub_rn(box.hi[v], box.lo[v]));
+    double* tv = cheb + (size_t)v * ne * tpb + tid;
+    tv[0] = 1.0;
+    if (eta >= 1) tv[tpb] = xi;
+    double tm1 = 1.0, tc = xi;
+    for (int e = 2; e <= eta; ++e) {
+      const double tn = __dsub_rn(__dmul_rn(__dmul_rn(2.0, xi), tc), tm1);
+      tm1 = tc;
+      tc = tn;
+      tv[(size_t)e * tpb] = tc;
+    }
+  }
+  const int l0 = blockIdx.y * 32;
   const int l1 = min(p, l0 + 32);
   for (int l = l0; l < l1; ++l) {
     const uint2 pr = pairs[l];
@@ -61,16 +84,7 @@ __global__ void k_basis(int n, int n_pad, int p, const uint2* __restrict__ pairs
     for (int a = 0; a < nz; ++a) {
       const uint32_t byte = ((a < 4 ? pr.x >> (8 * a) : pr.y >> (8 * (a - 4)))) & 0xffu;
       const int v = (int)(byte >> 4), e = (int)(byte & 15u);
-      const double y = (v == 0) ? t[i] : x[(size_t)(v - 1) * n + i];
-      const double xi = __ddiv_rn(__dsub_rn(__dmul_rn(2.0, y), __dadd_rn(box.lo[v], box.hi[v])),
-                                  __dsub_rn(box.hi[v], box.lo[v]));
-      double tm1 = 1.0, tc = xi;
-      for (int q = 1; q < e; ++q) {
-        const double tn = __dsub_rn(__dmul_rn(__dmul_rn(2.0, xi), tc), tm1);
-        tm1 = tc;
-        tc = tn;
-      }
-      val = __dmul_rn(val, tc);
+      val = __dmul_rn(val, cheb[((size_t)v * ne + e) * tpb + tid]);
     }
     B[(size_t)l * n_pad + i] = val;
     if (split) {
@@ -103,7 +117,14 @@ void launch_basis(const ModelHost& m, const GridHost& g, const ProblemDev& P, bo
     box.lo[v] = g.lo[v];
     box.hi[v] = g.hi[v];
   }
-  dim3 grid((P.n + 127) / 128, (P.p + 31) / 32);
-  k_basis<<<grid, 128, 0, st>>>(P.n, P.n_pad, P.p, P.pairs, P.nnz, P.t, P.x, box, P.B, P.Bhi,
-                                P.Blo, mixed ? 1 : 0);
+  const int dp = m.d + 1, eta = P.eta < 1 ? 1 : P.eta;
+  // Chebyshev table of T_0..T_eta per variate and thread, within 48 KB
+  int tpb = 128;
+  while (tpb > 32 && (size_t)dp * (eta + 1) * tpb * sizeof(double) > 48 * 1024) tpb >>= 1;
+  const size_t smem = (size_t)dp * (eta + 1) * tpb * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_basis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((P.n + tpb - 1) / tpb, (P.p + 31) / 32);
+  k_basis<<<grid, tpb, smem, st>>>(P.n, P.n_pad, P.p, dp, eta, P.pairs, P.nnz, P.t, P.x, box, P.B,
+                                   P.Bhi, P.Blo, mixed ? 1 : 0);
 }
