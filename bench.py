@@ -41,10 +41,10 @@ FLOPS_PER_PATH_STEP = 300.0
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of one path-kernel launch per point, from the ncu
 # capture summarised in profiles/k_paths_d10_dense_n800.md (n = 800 points:
-# 149.2 KB read, 0 B written: the partial sums stay in L2), scaled to a
+# 145.4 KB read, 0 B written: the partial sums stay in L2), scaled to a
 # launch over n points (the kernel reads the points and coefficients and
 # writes one partial sum per (point, chunk), both proportional to n).
-PATH_TRAFFIC_BYTES_PER_POINT = (149248.0 + 0.0) / 800.0
+PATH_TRAFFIC_BYTES_PER_POINT = (145408.0 + 0.0) / 800.0
 
 
 def env_rank():
@@ -443,7 +443,7 @@ def run_ours(args):
               "resid_l2": list(r1.resid_l2[:cfg["K_it"]]), "status": r1.status}
     # the other configured workloads (whole solves, graph replay, device time)
     others = {}
-    for name, prec in (("c1", "fp64"), ("c2", "mixed"), ("c3", "mixed")):
+    for name, prec in (() if args.no_others else (("c1", "fp64"), ("c2", "mixed"), ("c3", "mixed"))):
         wc = workloads.config(name)
         ws = G.Solver(wc, precision=prec, device=local)
         ws.solve(use_graph=1)
@@ -510,6 +510,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--case", default="bench", choices=["bench", "profile", "profile_tree"])
+    ap.add_argument("--no-others", action="store_true", help="skip the other configured workloads")
     ap.add_argument("--serving-requests", type=int, default=100,
                     help="requests of the Poisson serving mix (0: skip; 2000: the full mix)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
