@@ -136,9 +136,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(cfg, budget_s=12.0):
+def cpu_oracle_rate(cfg, budget_s=12.0, gpu_c=None):
     """The oracle (FP64, C, threads over points) on this host's cores: one
-    iteration's corrections at a bounded sample of points; path-steps/s."""
+    iteration's corrections at a bounded sample of points; path-steps/s.
+    With gpu_c (the GPU's corrections of the same iteration from the same
+    coefficients, at all points), also the largest difference between the
+    two at the sampled points."""
     import numpy as np
     from oracle import bsde_oracle as O
     nth = os.cpu_count() or 1
@@ -153,13 +156,20 @@ def cpu_oracle_rate(cfg, budget_s=12.0):
     npts = min(npts, cfg["n"])
     idx = np.arange(npts)
     t0 = time.perf_counter()
-    O.correction(cfg, nu, alpha, 0, idx, t[idx], x[:, idx], nthreads=nth)
+    c_or = O.correction(cfg, nu, alpha, 0, idx, t[idx], x[:, idx], nthreads=nth)
     el = time.perf_counter() - t0
     steps = npts * cfg["M"] * cfg["N"]
-    return {"value": steps / el, "unit": UNIT, "cores": nth, "kind": "oracle",
-            "sample": "one Picard iteration, corrections c_i at %d of the %d points (M=%d paths, N=%d "
-                      "steps each, p=%d), FP64 C oracle, %.1f s" % (npts, cfg["n"], cfg["M"], cfg["N"],
-                                                                    len(nu), el)}
+    out = {"value": steps / el, "unit": UNIT, "cores": nth, "kind": "oracle",
+           "sample": "one Picard iteration, corrections c_i at %d of the %d points (M=%d paths, N=%d "
+                     "steps each, p=%d), FP64 C oracle, %.1f s" % (npts, cfg["n"], cfg["M"], cfg["N"],
+                                                                   len(nu), el)}
+    if gpu_c is not None:
+        err = float(np.max(np.abs(np.asarray(gpu_c)[idx] - c_or)))
+        mag = float(np.max(np.abs(c_or)))
+        out["parity_vs_gpu"] = {"points": int(npts), "gpu_precision": "mixed",
+                                "max_abs_err_c": err, "max_abs_c": mag,
+                                "max_err_relative_to_max_c": err / max(1.0, mag)}
+    return out
 
 
 def run_reference(args):
@@ -456,7 +466,16 @@ def run_ours(args):
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     launch_steps = cfg["n"] * cfg["M"] * cfg["N"]
     achieved = FLOPS_PER_PATH_STEP * launch_steps / (path_ms * 1e-3) / 1e12 if path_ms > 0 else None
-    cpu = cpu_oracle_rate(cfg, budget_s=args.cpu_budget) if not args.no_cpu else None
+    cpu = None
+    if not args.no_cpu:
+        # the GPU's corrections of the iteration the oracle times (same
+        # points, same coefficients), for the parity figure of the line
+        pc = G.Solver(cfg, precision="mixed", device=local)
+        a0 = np.zeros(pc.basis_size())
+        a0[0] = 5.0
+        _, _, c_gpu, _ = pc.iterate(0, a0)
+        pc.close()
+        cpu = cpu_oracle_rate(cfg, budget_s=args.cpu_budget, gpu_c=c_gpu)
     serving = run_serving_suite(args.serving_requests) if args.serving_requests > 0 else None
     rep0 = reps[-1]
     line = {
