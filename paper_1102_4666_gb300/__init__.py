@@ -36,6 +36,7 @@ PREC_MIXED = 1
 VOL_CONST, VOL_ABS_TANH, VOL_SIN_TANH, VOL_DUPIRE = 0, 1, 2, 3
 PAYOFF_PUT, PAYOFF_CALL = 0, 1
 OBSTACLE_PAYOFF, OBSTACLE_RAW = 0, 1
+POLICY_FIFO, POLICY_SHORTEST, POLICY_RESPONSE_RATIO = 0, 1, 2
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -413,12 +414,18 @@ def basis_indices(d, eta, q=1.0):
 
 
 class Server:
-    """Continuous-batching server of the C ABI (bsde_server_*)."""
+    """Continuous-batching server of the C ABI (bsde_server_*): up to
+    max_slots requests resident at once (each a captured graph of its whole
+    solve on a stream of its own), admitted while they fit mem_budget bytes
+    (0: no limit) in the order of the policy: "fifo", "shortest" (fewest
+    path-steps K_it n M N first) or "response_ratio" (highest
+    (wait + service) / service first)."""
 
     def __init__(self, device=0, max_slots=16, mem_budget=0, precision="mixed", policy="fifo"):
         o = bsde_server_opts()
         o.device, o.max_slots, o.mem_budget = device, max_slots, mem_budget
-        o.policy = {"fifo": 0, "shortest": 1, "response_ratio": 2}[policy]
+        o.policy = {"fifo": POLICY_FIFO, "shortest": POLICY_SHORTEST,
+                    "response_ratio": POLICY_RESPONSE_RATIO}[policy]
         o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
         h = ctypes.c_void_p()
         rc = lib().bsde_server_create(ctypes.byref(h), ctypes.byref(o))
