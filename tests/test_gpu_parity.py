@@ -370,6 +370,39 @@ def test_checkpoint_resume_reproduces_the_run(G):
     assert np.array_equal(full, resumed)
 
 
+def test_factorisation_groups_do_not_change_the_run(G):
+    """A d = 10 degree-4 basis (p = 1365): the Gram factors and inverses of
+    one group of iterations hold 8 iterations (256 MiB), so a 10-iteration
+    solve factorises in two groups; it must equal the same run done as two
+    solves of 5 iterations (one group each, resumed from the coefficients)."""
+    cfg = workloads.config("c4", n=2800, M=16, N=3, eta=4, K_it=10, **{"lambda": 1.0})
+    s = solver(G, cfg, "mixed")
+    r = s.solve()
+    full = s.coeffs()
+    s.solve(K_it=5)
+    half = s.coeffs()
+    s.close()
+    s2 = solver(G, cfg, "mixed")
+    s2.set_coeffs(half)
+    s2.solve(K_it=5, k_start=5)
+    resumed = s2.coeffs()
+    s2.close()
+    assert r.status == G.OK and np.array_equal(full, resumed)
+
+
+def test_maximum_iteration_count(G):
+    """K_it = 64 (the largest the report holds): every per-iteration entry is
+    written, and the iteration converges at the paper's omega = 1."""
+    cfg = workloads.config("c1", n=100, M=100, N=5, eta=3, K_it=64)
+    s = solver(G, cfg, "mixed")
+    r = s.solve()
+    s.close()
+    assert r.status == G.OK and r.K_it == 64
+    res = np.array(r.resid_l2[:64])
+    assert np.all(np.isfinite(res)) and np.all(res > 0)
+    assert np.all(np.array(r.price_iter[:64]) != 0.0)
+
+
 def test_errors_are_status_codes(G):
     cfg = workloads.config("c3", n=20, M=10, N=3, eta=4)  # p = 210 > n/2
     s = solver(G, cfg, "fp64")
@@ -392,6 +425,15 @@ def test_errors_are_status_codes(G):
     s3 = solver(G, bad, "fp64")
     assert s3.solve(check=False).status == G.ERR_INVALID_ARG
     s3.close()
+    # empty inputs: no paths, no steps, K_it beyond the report
+    s6 = solver(G, workloads.config("c1", n=100, M=10, N=3, eta=2, K_it=1), "mixed")
+    for kw in (dict(M=0), dict(N_steps=0), dict(K_it=65)):
+        p = G.solve_params(s6.cfg)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        assert G.lib().bsde_solve(s6.h, __import__("ctypes").byref(p),
+                                  __import__("ctypes").byref(G.bsde_report())) == G.ERR_INVALID_ARG
+    s6.close()
     # the dense evaluation forced where it does not apply: a full correlation
     # matrix, and a degree-5 basis with FP64 paths (tree kernels are FP32)
     full = _case("d3_full_corr")
