@@ -112,6 +112,7 @@ CASES = {
     # (p = 1365) and degree 5 at d = 5 (p = 462)
     "d10_degree4": ("c4", dict(n=2800, M=16, N=5, eta=4)),
     "d5_degree5": ("c3", dict(n=940, M=40, N=6, eta=5)),
+    "d5_degree6": ("c3", dict(n=1900, M=24, N=4, eta=6)),
     # a full correlation matrix (no constant correlation): the general
     # triangular product L Z in the Euler step and the correlation-weighted
     # cross terms of the per-thread table evaluation
