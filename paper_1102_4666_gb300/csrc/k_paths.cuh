@@ -13,19 +13,22 @@
 // every normal is a compile-time offset.  The time factors of the local
 // volatility, the coefficients alpha and the multi-index table are staged
 // in shared memory once per CTA.  The random time tau falls inside step s*;
-// the main loop only records the states before and after step s* (for the
-// Chebyshev-table kernels behind a warp vote, so that a warp none of whose
-// paths is at its step s* skips the copies), and X_tau is drawn after the
-// loop through a Brownian bridge.  u^k and its derivatives at (tau, X_tau)
-// and u^k(T, X_T) come from per-thread Chebyshev tables in shared memory
-// (layout [slot][thread], conflict-free), or, when the basis has total
-// degree <= 3 (EV = EV_DENSE3; <= 4 for d <= 5, EV = EV_DENSE4), from the
-// monomial coefficients beta of u^k (converted from the Chebyshev
-// coefficients once per iteration) by unrolled symmetric-tensor loops whose
-// indices are compile-time constants, so that u, grad u and the Hessian stay
-// in registers.  Per-path samples are accumulated in FP64; the CTA
-// reduces them by a fixed warp-shuffle tree into partial[i][chunk], so the
-// result does not depend on scheduling.
+// the main loop only records the states before and after step s* (behind a
+// warp vote where registers allow, so that a warp none of whose paths is at
+// its step s* skips the copies), and X_tau is drawn after the loop through a
+// Brownian bridge.  u^k and its derivatives at (tau, X_tau) and u^k(T, X_T)
+// come from per-thread Chebyshev tables in shared memory (layout
+// [slot][thread], conflict-free), or from the monomial coefficients beta of
+// u^k (converted from the Chebyshev coefficients once per iteration, constant
+// correlation only): Horner loops for total degree <= 3 (EV_DENSE3) and for
+// degree 4 at d <= 5 (EV_DENSE4), a compile-time recursion over the prefix
+// tree of variate multisets for degree 4 at d >= 6 and degrees 5 and 6 at
+// d <= 5 (EV_TREE4..6, FP32 paths); every index is a compile-time constant,
+// so u and its derivatives stay in registers.  The warps of a CTA enter the
+// larger of these evaluations together (a barrier before them) to share
+// their instruction fetches.  Per-path samples are accumulated in FP64; the
+// CTA reduces them by a fixed warp-shuffle tree into partial[i][chunk], so
+// the result does not depend on scheduling.
 #pragma once
 #include "common.cuh"
 
