@@ -301,7 +301,8 @@ BSDE_API int bsde_corrections_noalloc(const bsde_sigma* sigma, double r, const b
  * uneven d, n, M, N and degree are admitted while device memory (the
  * server's budget) and slots allow; each keeps its coefficients and points
  * resident across its Picard iterations; the iterations of all admitted
- * requests run concurrently on the device; a finished request frees its
+ * requests run concurrently on the device (requests with less work than the
+ * average so far on high-priority streams); a finished request frees its
  * slot for the next one in the queue.
  * ---------------------------------------------------------------------- */
 typedef struct bsde_server bsde_server;

@@ -39,6 +39,7 @@ struct Req {
   double t_submit = 0.0, t_done = 0.0;
   size_t bytes = 0;
   double work = 0.0;  // K_it n M N, the shortest-first key
+  int prio = 0;       // 1: admitted on a high-priority stream
   std::unique_ptr<Problem> prob;
   cudaStream_t stream = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -59,7 +60,12 @@ struct bsde_server {
   std::deque<std::unique_ptr<Req>> queue;
   std::vector<std::unique_ptr<Req>> running;
   std::map<uint64_t, std::unique_ptr<Req>> done;
-  std::vector<cudaStream_t> free_streams;
+  // streams of finished requests, by priority: requests with less work than
+  // the average so far run on high-priority streams, so that their kernels
+  // take the next free CTA slots ahead of the long requests' path kernels
+  std::vector<cudaStream_t> free_streams[2];  // [0] normal, [1] high priority
+  double work_sum = 0.0;
+  uint64_t work_count = 0;
   size_t used_bytes = 0;
   std::vector<uint64_t> admitting;  // ids popped from the queue, not yet in running/done
   std::vector<double> latencies_ms;
@@ -102,12 +108,18 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
   used_bytes += req->bytes;
   if (busy_since < 0) busy_since = now_s();
   cudaStream_t st;
-  if (!free_streams.empty()) {
-    st = free_streams.back();
-    free_streams.pop_back();
+  work_sum += req->work;
+  ++work_count;
+  const int hi = req->work < work_sum / (double)work_count ? 1 : 0;
+  if (!free_streams[hi].empty()) {
+    st = free_streams[hi].back();
+    free_streams[hi].pop_back();
   } else {
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    int lo_p = 0, hi_p = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_p, &hi_p);
+    cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi ? hi_p : lo_p);
   }
+  req->prio = hi;
   req->stream = st;
   admitting.push_back(req->id);
   lk.unlock();
@@ -130,7 +142,7 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
     req->t_done = now_s();
     P.release(al, st);
     used_bytes -= req->bytes;
-    free_streams.push_back(st);
+    free_streams[req->prio].push_back(st);
     done[req->id] = std::move(req);
     cv_done.notify_all();
     return true;
@@ -164,7 +176,7 @@ void bsde_server::loop() {
       r->e0 = r->e1 = nullptr;
       lk.lock();
       used_bytes -= r->bytes;
-      free_streams.push_back(r->stream);
+      free_streams[r->prio].push_back(r->stream);
       latencies_ms.push_back((r->t_done - r->t_submit) * 1e3);
       if (r->rc == BSDE_OK) path_steps += r->rep.path_steps;
       ++completed;
@@ -314,7 +326,8 @@ void bsde_server_destroy(bsde_server* s) {
   }
   s->worker.join();
   cudaSetDevice(s->opts.device);
-  for (auto st : s->free_streams) cudaStreamDestroy(st);
+  for (auto& pool : s->free_streams)
+    for (auto st : pool) cudaStreamDestroy(st);
   delete s;
 }
 
