@@ -91,6 +91,27 @@ def test_c1_mixed_price_delta(G):
     assert abs(rep.delta[0] - ref["delta"][0]) <= 1e-4 * abs(ref["delta"][0])
 
 
+@pytest.mark.parametrize("name,K_it", [("c3", 10), ("c4", 4)])
+def test_full_size_mixed_price_delta_against_fp64(G, name, K_it):
+    """The d = 5 and d = 10 American basket puts at their full sizes with the
+    paper's penalty weight omega = 1: the mixed-precision solve's price and
+    deltas at (0, x0) within 1e-4 relative of the FP64 solve (the FP64 path is
+    pinned to the oracle at 1e-9 by the tests above; a full FP64 oracle solve
+    at these sizes would take hours on the CPU).  Both use the same random
+    numbers, so the difference is the FP32 arithmetic alone."""
+    cfg = workloads.config(name, K_it=K_it, **{"lambda": 1.0})
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = solver(G, cfg, prec)
+        r = s.solve(use_graph=1)
+        s.close()
+        assert r.status == G.OK
+        out[prec] = (r.price, np.array(r.delta[:cfg["d"]]))
+    (pm, dm), (pf, df) = out["mixed"], out["fp64"]
+    assert abs(pm - pf) <= 1e-4 * abs(pf)
+    assert np.max(np.abs(dm - df)) <= 1e-4 * np.max(np.abs(df))
+
+
 # ---------------------------------------------------------------------------
 # one iteration from the same alpha^k (teacher forcing)
 # ---------------------------------------------------------------------------
