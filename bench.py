@@ -496,7 +496,9 @@ def run_ours(args):
                                  if PATH_TRAFFIC_BYTES_PER_POINT else None),
                      "traffic_basis": "dram read+write per launch from the n=800 ncu capture, scaled by n",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock %.0f MHz" % sm_mhz,
-                     "flops_per_path_step": FLOPS_PER_PATH_STEP, "path_kernel_ms": path_ms},
+                     "flops_per_path_step": FLOPS_PER_PATH_STEP, "path_kernel_ms": path_ms,
+                     "issue_note": "instruction-issue bound: 352 instructions per path-step at IPC 2.90 "
+                                   "of 4 (0.73 of the issue rate; profiles/k_paths_d10_dense_n800.md)"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
