@@ -1,0 +1,70 @@
+"""Host-side logic that needs no GPU: the autotuner's problem-class key and
+JSON cache, the seeded request mix of the serving benchmark, and the
+benchmark's arrival stream and weak-scaling arithmetic."""
+import json
+import math
+
+import pytest
+
+import workloads
+
+
+def test_autotune_key_buckets_problem_classes():
+    from paper_1102_4666_gb300 import autotune
+    c4 = workloads.config("c4")
+    # the bucket is the next power of two of M: 3000 and 4000 share a class
+    assert autotune.key(workloads.config("c4", M=3000), "mixed") == autotune.key(c4, "mixed")
+    assert autotune.key(workloads.config("c4", M=5000), "mixed") != autotune.key(c4, "mixed")
+    assert autotune.key(c4, "fp64") != autotune.key(c4, "mixed")
+    assert autotune.key(workloads.config("c4", eta=4), "mixed") != autotune.key(c4, "mixed")
+
+
+def test_autotune_cache_round_trip(tmp_path, monkeypatch):
+    from paper_1102_4666_gb300 import autotune
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("BSDE_TUNE_CACHE", str(path))
+    c3 = workloads.config("c3")
+    assert autotune.lookup(c3, "mixed") is None
+    path.write_text(json.dumps({autotune.key(c3, "mixed"): {"shape": [256, 2], "ms_paths": 1.0}}))
+    assert autotune.lookup(c3, "mixed") == (256, 2)
+    assert autotune.lookup(workloads.config("c4"), "mixed") is None
+
+
+def test_serving_mix_is_seeded_and_respects_its_ranges():
+    a = workloads.serving_mix(300, seed=7)
+    b = workloads.serving_mix(300, seed=7)
+    assert [r["n"] for r in a] == [r["n"] for r in b] and [r["eta"] for r in a] == [r["eta"] for r in b]
+    assert [r["n"] for r in a] != [r["n"] for r in workloads.serving_mix(300, seed=8)]
+    for r in a:
+        assert r["d"] in (1, 2, 5, 10)
+        assert 200 <= r["n"] <= 4000 and 500 <= r["M"] <= 8000 and 2 <= r["eta"] <= 6
+        assert 80.0 <= r["K"] <= 120.0 and 0.25 <= r["T"] <= 2.0
+        assert r["lambda"] in (0.0, 100.0)
+        assert 2 * workloads.basis_size(r["d"], r["eta"]) <= r["n"]  # p <= n / 2
+    assert {r["d"] for r in a} == {1, 2, 5, 10}
+
+
+def test_basis_size_is_the_binomial_coefficient():
+    assert workloads.basis_size(10, 3) == 364 and workloads.basis_size(5, 4) == 210
+    assert workloads.basis_size(1, 6) == 28
+    for d in range(1, 11):
+        for eta in range(0, 7):
+            assert workloads.basis_size(d, eta) == math.comb(d + 1 + eta, eta)
+
+
+def test_arrival_stream_is_seeded_and_poisson_like():
+    import bench
+    t = bench.arrival_times(4000, 20.0, 7)
+    assert t == bench.arrival_times(4000, 20.0, 7)
+    gaps = [b - a for a, b in zip([0.0] + t[:-1], t)]
+    assert all(g > 0 for g in gaps)
+    mean = sum(gaps) / len(gaps)
+    assert abs(mean - 1 / 20.0) < 4 * (1 / 20.0) / math.sqrt(len(gaps))  # 4 standard errors
+    assert abs(sorted(gaps)[len(gaps) // 2] - math.log(2) / 20.0) < 0.1 / 20.0  # exponential median
+
+
+def test_weak_scaling_value_single_rank():
+    import bench
+    value, ms = bench.weak_scaling_value(2000.0, 4, 1.92e10)
+    assert ms == 2000.0
+    assert value == pytest.approx(4 * 1.92e10 / 2.0)
