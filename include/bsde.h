@@ -5,7 +5,7 @@
  * American options" (arXiv:1102.4666).
  *
  * The library prices and hedges European and American (penalised) basket
- * options in a d-dimensional local-volatility model (Section 4) by solving
+ * options in a d-dimensional local-volatility model (Section 5) by solving
  * the BSDE  -dY = f(t,X,Y,Z) dt - Z dW,  Y_T = Phi(X_T)  (eq. eqs1) with the
  * driver f(t,x,y) = -r y + lambda (Phi(x) - y)^+ (eq. bsde-penal-2).  Every
  * step of Algorithm 2 runs in CUDA kernels: the random points, the Monte
@@ -63,12 +63,12 @@ extern "C" {
 #define BSDE_PREC_MIXED 1 /* FP32 paths/basis/driver, FP64 per-point sums,
                              3xTF32 tensor-core Gram, FP64 Cholesky       */
 
-/* volatility families sigma_j(t, x) of the model eq. (4), Section 4.1, with
+/* volatility families sigma_j(t, x) of the model eq. eq4, Section 5.1, with
  * sigma_ij = sigma_j(t, x) L_ij and L the Cholesky factor of the correlation */
 #define BSDE_VOL_CONST 0    /* sigma_j = a_j                                 */
 #define BSDE_VOL_ABS_TANH 1 /* a_j + b e^{-t} |tanh(x_j - kappa_j)|          */
 #define BSDE_VOL_SIN_TANH 2 /* a_j + b sin(j + t) tanh(x_j - kappa_j), j=1..d */
-#define BSDE_VOL_DUPIRE 3   /* eq. vol_locale of Section 5.3 on S_j = e^{x_j} */
+#define BSDE_VOL_DUPIRE 3   /* eq. vol_locale of Section 6.3 on S_j = e^{x_j} */
 
 #define BSDE_PAYOFF_PUT 0  /* (K - sum_j w_j S_j)^+, eq. put_payoff            */
 #define BSDE_PAYOFF_CALL 1 /* (sum_j w_j S_j - K)^+, eq. call_payoff           */
@@ -106,8 +106,8 @@ BSDE_API void bsde_destroy(bsde_ctx* ctx);
  * ctx == NULL, the message of the last failing bsde_create in this thread. */
 BSDE_API const char* bsde_last_error(const bsde_ctx* ctx);
 
-/* Volatility and correlation of the model eq. (4) (Section 4.1) with the
- * correlated Brownian motion of Section 5.2 (C = L L^*). */
+/* Volatility and correlation of the model eq. eq4 (Section 5.1) with the
+ * correlated Brownian motion of Section 6.2 (C = L L^*). */
 typedef struct {
   int d;               /* number of assets, 1..BSDE_MAX_D                    */
   int kind;            /* BSDE_VOL_*                                          */
@@ -122,7 +122,7 @@ typedef struct {
   const double* div;   /* optional d dividend rates delta_j (NULL: 0)        */
 } bsde_sigma;
 
-/* Payoff Phi of the option (Section 5.2.1) on S = e^x. */
+/* Payoff Phi of the option (Section 6.2.1) on S = e^x. */
 typedef struct {
   int kind;               /* BSDE_PAYOFF_*                                   */
   double K;               /* strike                                          */
@@ -132,8 +132,8 @@ typedef struct {
 } bsde_payoff;
 
 /* Penalisation of eq. bsde-penal-2: lambda = 0 gives the European option
- * (Section 4.4), lambda > 0 the penalised approximation of the American
- * option (Section 4.3). */
+ * (Section 5.5), lambda > 0 the penalised approximation of the American
+ * option (Section 5.4). */
 typedef struct {
   double lambda;
   int obstacle; /* BSDE_OBSTACLE_* */

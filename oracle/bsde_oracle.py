@@ -11,7 +11,7 @@ plain C file oracle.c, the rest is numpy:
     numpy.linalg.lstsq (an SVD-based LAPACK solver, in the role the paper
     gives to LAPACK's dgelsy, Section 3.2.2),
   * the Picard loop of Algorithm 2 and the price / delta outputs
-    (Section 4.3: V = Y = u, Delta = grad_x V).
+    (Section 5.3: V = Y = u, Delta = grad_x V).
 """
 import ctypes
 import math
@@ -373,7 +373,7 @@ def iteration(cfg, nu, alpha, k, nthreads=None):
 
 
 def price_delta(cfg, nu, alpha, t0=0.0, S0=None):
-    """Price u(t0, log S0) and delta dV/dS_j = (du/dx_j)/S_j (Section 4.3,
+    """Price u(t0, log S0) and delta dV/dS_j = (du/dx_j)/S_j (Sections 5.1 and 5.3,
     Delta = grad_x V, read on the price scale)."""
     S0 = cfg["S0"] if S0 is None else S0
     x0 = np.log(np.asarray(S0, dtype=np.float64)).reshape(cfg["d"], 1)

@@ -1,9 +1,9 @@
 """Reference prices used to pin the oracle end to end (test infrastructure).
 
   * Black-Scholes closed form of the European put/call and its delta (the
-    omega = 0 case of Section 4.4 in one dimension with constant volatility);
+    omega = 0 case of Section 5.5 in one dimension with constant volatility);
   * the Cox-Ross-Rubinstein binomial tree for European and American puts
-    (brute force for the American price of Section 4.2);
+    (brute force for the American price of Section 5.2);
   * an implicit finite-difference solver of the penalised one-dimensional PDE
     d_t u + A u - r u + lambda (Phi - u)^+ = 0 (the PDE of eq. bsde-penal-2
     through the link of Section 2.2), i.e. the fixed point the Picard

@@ -20,7 +20,7 @@
  * easy as 1, 2, 3", SC'11, Section 3): ten rounds of
  *   (c0,c1,c2,c3) -> (hi(M1*c2)^c1^k0, lo(M1*c2), hi(M0*c0)^c3^k1, lo(M0*c0))
  * with the key bumped by the Weyl constants between rounds.  The paper's
- * DCMT generator (Section 3.3) is replaced by this counter-based generator,
+ * DCMT generator (Section 4.4) is replaced by this counter-based generator,
  * which gives independent streams without any creation step.
  * ---------------------------------------------------------------------- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
@@ -56,7 +56,7 @@ void orc_box_muller(uint32_t w0, uint32_t w1, double* z0, double* z1) {
   *z1 = radius * sin(two_pi * u1);
 }
 
-/* Cholesky-Banachiewicz, C = L L^T (Section 5.2: the correlation matrix
+/* Cholesky-Banachiewicz, C = L L^T (Section 6.2: the correlation matrix
  * C = (rho 1_{i!=j} + 1_{i=j}) is factored as L L^*).  Returns 0 on success,
  * -1 if C is not positive definite. */
 int orc_cholesky(int d, const double* C, double* L) {
@@ -134,10 +134,10 @@ double orc_sigma(const orc_model* m, int j, double t, double xj) {
     case ORC_VOL_ABS_TANH:
       return m->va[j] + m->vb * exp(-t) * fabs(tanh(xj - m->kappa[j]));
     case ORC_VOL_SIN_TANH:
-      /* assets are numbered from 1 (Section 4.1) */
+      /* assets are numbered from 1 (Section 5.1) */
       return m->va[j] + m->vb * sin((double)(j + 1) + t) * tanh(xj - m->kappa[j]);
     case ORC_VOL_DUPIRE: {
-      /* eq. vol_locale (Section 5.3), written on the price S = e^x */
+      /* eq. vol_locale (Section 6.3), written on the price S = e^x */
       double S = exp(xj);
       double dev = S * exp(m->r * t) - m->s_dupire;
       return 0.6 * (1.2 - exp(-0.1 * t) * exp(-0.001 * dev * dev)) * exp(-0.05 * sqrt(t));
@@ -147,7 +147,7 @@ double orc_sigma(const orc_model* m, int j, double t, double xj) {
   }
 }
 
-/* basket payoff, eq. put_payoff / call_payoff (Section 5.2.1) on x = log S */
+/* basket payoff, eq. put_payoff / call_payoff (Section 6.2.1) on x = log S */
 double orc_payoff(const orc_model* m, const double* x) {
   double basket = 0.0;
   for (int j = 0; j < m->d; ++j) basket += m->w[j] * exp(x[j]);
@@ -250,8 +250,8 @@ void orc_basis_eval(const orc_model* m, const orc_basis* b, const double* alpha,
  *                  + sum b_j(phi(s), X_phi(s)) d_j u(s, X_s)
  * (Section 3.1), the penalised driver f(t,x,y) = -r y + lambda (Phi(x) - y)^+
  * of eq. bsde-penal-2 ((Y - Phi)^- = (Phi - Y)^+), and the log-price Euler
- * scheme eqs3 with the model eq. (4): b_j = r - delta_j - sigma_j^2/2,
- * A = diag(sigma) C diag(sigma), W increments sqrt(h) L G (Section 5.2).
+ * scheme eqs3 with the model eq. eq4: b_j = r - delta_j - sigma_j^2/2,
+ * A = diag(sigma) C diag(sigma), W increments sqrt(h) L G (Section 6.2).
  * The N Euler steps run on the regular grid of [t_i, T].  U is one 32-bit
  * word w: U = (s* + theta)/N with s* = floor(w N / 2^32) and theta the
  * remaining fraction; X^N_tau is the Euler interpolation eqs3 inside step

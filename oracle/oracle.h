@@ -1,8 +1,8 @@
 /*
  * oracle.h -- plain FP64 CPU restatement of the Picard-iteration /
  * adaptive-control-variate BSDE solver of Labart & Lelong ("A Parallel
- * Algorithm for solving BSDEs", Algorithm 2 of Section 3 and the pricing
- * model of Section 4).
+ * Algorithm for solving BSDEs", Algorithm 2 of Section 4.1 and the pricing
+ * model of Section 5).
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
  * cpu_baseline leg of bench.py may load this code.  It shares no code with
@@ -28,11 +28,11 @@
 #define ORC_TAG_Z 3u
 #define ORC_TAG_B 4u
 
-/* volatility families (Section 4.1 eq. (4) with sigma_ij = sigma_i L_ij) */
+/* volatility families (Section 5.1 eq. eq4 with sigma_ij = sigma_i L_ij) */
 #define ORC_VOL_CONST 0    /* sigma_j = a_j                                   */
 #define ORC_VOL_ABS_TANH 1 /* a_j + b e^{-t} |tanh(x_j - kappa_j)|            */
 #define ORC_VOL_SIN_TANH 2 /* a_j + b sin(j + t) tanh(x_j - kappa_j), j=1..d  */
-#define ORC_VOL_DUPIRE 3   /* eq. vol_locale of Section 5.3                   */
+#define ORC_VOL_DUPIRE 3   /* eq. vol_locale of Section 6.3                   */
 
 #define ORC_PAYOFF_PUT 0
 #define ORC_PAYOFF_CALL 1

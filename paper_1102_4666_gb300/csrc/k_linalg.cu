@@ -6,7 +6,7 @@
 // dgelsy; here the Gram matrix is factored by an FP64 Cholesky on the GPU,
 // with an optional FP64 iterative refinement of the normal equations.
 // Also: the per-point reduction of eq. chat, the coefficient update and the
-// price / delta read-out of Section 4.3.
+// price / delta read-out of Section 5.3.
 #include "common.cuh"
 
 namespace {
@@ -347,7 +347,7 @@ struct EvalArgs {
   double ctr[BSDE_DMAX + 1], sc[BSDE_DMAX + 1];
 };
 
-// u and du/dx_j at query points (Section 4.3: price V = u, Delta = grad_x V):
+// u and du/dx_j at query points (Section 5.3: price V = u, Delta = grad_x V):
 // one CTA per point, threads over basis functions, fixed-order reduction.
 __global__ void __launch_bounds__(256) k_eval(const __grid_constant__ EvalArgs ea,
                                               const double* __restrict__ alpha,

@@ -69,7 +69,7 @@ void Allocator::put(void* p, cudaStream_t st) {
 
 static bool is_fin(double v) { return std::isfinite(v); }
 
-// Cholesky-Banachiewicz of the d x d correlation (C = L L^*, Section 5.2)
+// Cholesky-Banachiewicz of the d x d correlation (C = L L^*, Section 6.2)
 static bool cholesky_host(int d, const double* C, double* L) {
   for (int i = 0; i < d * d; ++i) L[i] = 0.0;
   for (int i = 0; i < d; ++i)

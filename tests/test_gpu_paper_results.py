@@ -1,5 +1,5 @@
 """End-to-end accuracy of the solver on the paper's own experiments
-(Section 5): the prices and deltas it prints (tests/golden/paper_results.txt).
+(Section 6): the prices and deltas it prints (tests/golden/paper_results.txt).
 
 The paper does not state its domain D; a box log S0 +- w with w of a few
 tenths (given per case) reproduces its numbers, whereas the wide box of the

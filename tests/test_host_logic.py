@@ -68,3 +68,16 @@ def test_weak_scaling_value_single_rank():
     value, ms = bench.weak_scaling_value(2000.0, 4, 1.92e10)
     assert ms == 2000.0
     assert value == pytest.approx(4 * 1.92e10 / 2.0)
+
+
+def test_paper_timing_workloads_follow_the_captions():
+    """The two timing-table workloads carry the captions' parameters (Section 6.4)."""
+    for name, d, M in (("paper_d3", 3, 1000), ("paper_d6", 6, 5000)):
+        c = workloads.config(name)
+        assert (c["d"], c["M"], c["N"], c["n"], c["eta"], c["K_it"]) == (d, M, 10, 2000, 3, 10)
+        assert (c["r"], c["K"], c["T"], c["rho"], c["lambda"], c["q"]) == (0.02, 95.0, 1.0, 0.0, 1.0, 1.0)
+        assert c["vol"] == {"kind": "const", "a": 0.2} and c["S0"] == [100.0] * d
+        t8, tbest, procs = workloads.PAPER_TIMING_SECONDS[name]
+        assert t8 > tbest and procs in (64, 256)
+    # the basis has d' = d + 1 variates: 35 functions at d = 3, 120 at d = 6
+    assert workloads.basis_size(3, 3) == 35 and workloads.basis_size(6, 3) == 120

@@ -133,7 +133,7 @@ def test_picard_residual_decreases():
 def test_penalised_price_lies_between_european_and_american():
     """The penalised BSDE (eq. bsde-penal-2) adds omega (Phi - Y)^+ >= 0 to
     the European driver and its solution increases to the American price as
-    omega grows (Section 4.3), so for omega = 1:
+    omega grows (Section 5.4), so for omega = 1:
     BS European <= Y^omega <= American (CRR tree, 2000 steps).  With
     r = 0.1 and S0 = 90 the bracket is wide (7.43 .. 10.43); the mean of the
     converged iterates also matches the finite-difference solution of the
