@@ -105,6 +105,59 @@ __device__ __forceinline__ uint4 philox_rk(const Args<R, D>& a, uint32_t c0, uin
   return make_uint4(c0, c1, c2, c3);
 }
 
+// Philox4x32-10 for a stream of counters (c0, c1, c2, c3) of which only c0
+// varies: the parts of rounds 1 and 2 that depend on c1, c2 and c3 alone are
+// computed once (PhiloxFixed) and the stream's blocks take 3 fewer wide
+// multiplies and xors each.  Same outputs as philox_rk.
+struct PhiloxFixed {
+  uint32_t n0;    // round 1: hi(c2 M1) ^ c1 ^ k0
+  uint32_t lo1;   // round 1: lo(c2 M1)
+  uint32_t hiA;   // round 2: hi(n0 M0)
+  uint32_t loA;   // round 2: lo(n0 M0)
+  uint32_t c3k;   // round 1: c3 ^ k1
+};
+
+template <typename R, int D>
+__device__ __forceinline__ PhiloxFixed philox_fix(const Args<R, D>& a, uint32_t c1, uint32_t c2,
+                                                  uint32_t c3) {
+  PhiloxFixed f;
+  const uint64_t p1 = (uint64_t)c2 * 0xCD9E8D57u;
+  f.n0 = (uint32_t)(p1 >> 32) ^ c1 ^ a.rk0[0];
+  f.lo1 = (uint32_t)p1;
+  const uint64_t pA = (uint64_t)f.n0 * 0xD2511F53u;
+  f.hiA = (uint32_t)(pA >> 32);
+  f.loA = (uint32_t)pA;
+  f.c3k = c3 ^ a.rk1[0];
+  return f;
+}
+
+template <typename R, int D>
+__device__ __forceinline__ uint4 philox_var(const Args<R, D>& a, const PhiloxFixed& f,
+                                            uint32_t c0) {
+  // round 1
+  const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u;
+  uint32_t c2 = (uint32_t)(p0 >> 32) ^ f.c3k;
+  uint32_t c3 = (uint32_t)p0;
+  // round 2 (c0 = f.n0, c1 = f.lo1)
+  const uint64_t p1 = (uint64_t)c2 * 0xCD9E8D57u;
+  c0 = (uint32_t)(p1 >> 32) ^ f.lo1 ^ a.rk0[1];
+  c2 = f.hiA ^ c3 ^ a.rk1[1];
+  uint32_t c1 = (uint32_t)p1;
+  c3 = f.loA;
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const uint64_t q0 = (uint64_t)c0 * 0xD2511F53u;
+    const uint64_t q1 = (uint64_t)c2 * 0xCD9E8D57u;
+    const uint32_t n0 = (uint32_t)(q1 >> 32) ^ c1 ^ a.rk0[r];
+    const uint32_t n2 = (uint32_t)(q0 >> 32) ^ c3 ^ a.rk1[r];
+    c1 = (uint32_t)q1;
+    c3 = (uint32_t)q0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
 // r = 1 / (e^{2 y} + 1), so that tanh(y) = 1 - 2 r, with y = x - kappa_j
 // (ABS: y = |x - kappa_j|, since |tanh(x - kappa)| = tanh(|x - kappa|))
 template <bool ABS, typename R, int D>
@@ -596,12 +649,13 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
       Xn[j] = x0[j];
     }
     const R nhh = R(-0.5) * h;
+    const PhiloxFixed pz = philox_fix(a, (uint32_t)m, (uint32_t)i, tagZ);
     for (int s0 = 0; s0 < a.N; s0 += G) {
       R z[G * D];  // normals of G steps, scaled by sqrt(h)
       const uint32_t blk0 = (uint32_t)(s0 / G) * (uint32_t)NB;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        const uint4 o = philox_rk(a, blk0 + b, (uint32_t)m, (uint32_t)i, tagZ);
+        const uint4 o = philox_var(a, pz, blk0 + b);
         Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1], bmk);
         Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3], bmk);
       }
