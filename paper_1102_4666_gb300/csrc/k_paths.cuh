@@ -679,6 +679,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
               if (hit) Xs[j] = X[j];
           }
           R pre = 0;  // running sum of the constant-correlation factor
+          float4 q4;  // (A_j, B_j, A_j+1, B_j+1) of the FP32 tanh families
 #pragma unroll
           for (int j = 0; j < D; ++j) {
             // correlated increment y = sqrt(h) (L Z)_j
@@ -691,7 +692,14 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
 #pragma unroll
               for (int q = 0; q <= j; ++q) y += a.L[j][q] * z[gs * D + q];
             }
-            const R sig = sigma_j<VK>(a, tabs, j, X[j]);
+            R sig;
+            if constexpr ((VK == VK_TANH || VK == VK_TANH_ABS) && sizeof(R) == 4) {
+              if ((j & 1) == 0) q4 = reinterpret_cast<const float4*>(tabs)[j >> 1];
+              const R r = tanh_r<VK == VK_TANH_ABS>(a, j, X[j]);
+              sig = (j & 1) ? (q4.z + q4.w * r) : (q4.x + q4.y * r);
+            } else {
+              sig = sigma_j<VK>(a, tabs, j, X[j]);
+            }
             // X + (r - delta_j - sigma^2/2) h + sigma y = X + h rd_j + sigma (y - h sigma / 2)
             X[j] = sig * (nhh * sig + y) + (h * a.rd[j] + X[j]);
           }
@@ -912,7 +920,9 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.tpb = tpb;
   a.ppt = ppt;
   a.chunks = P.chunks;
-  a.tab_stride = (m.vol_kind == 1 || m.vol_kind == 2) ? 2 * D : (D < 3 ? 3 : D);
+  // tanh families: (A_j, B_j) pairs, rows padded to 4 values (16 bytes in
+  // FP32) so that one 128-bit load fetches two assets' pairs
+  a.tab_stride = (m.vol_kind == 1 || m.vol_kind == 2) ? ((2 * D + 3) & ~3) : (D < 3 ? 3 : D);
   a.payoff = m.payoff;
   a.obstacle = m.obstacle;
   a.vol_sin = (m.vol_kind == 2) ? 1 : 0;
