@@ -41,10 +41,10 @@ FLOPS_PER_PATH_STEP = 300.0
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of one path-kernel launch per point, from the ncu
 # capture summarised in profiles/k_paths_d10_dense_n800.md (n = 800 points:
-# 145.2 KB read, 0 B written: the partial sums stay in L2), scaled to a
+# 144.6 KB read, 0 B written: the partial sums stay in L2), scaled to a
 # launch over n points (the kernel reads the points and coefficients and
 # writes one partial sum per (point, chunk), both proportional to n).
-PATH_TRAFFIC_BYTES_PER_POINT = (145152.0 + 0.0) / 800.0
+PATH_TRAFFIC_BYTES_PER_POINT = (144640.0 + 0.0) / 800.0
 
 
 def env_rank():
@@ -512,7 +512,7 @@ def run_ours(args):
                      "traffic_basis": "dram read+write per launch from the n=800 ncu capture, scaled by n",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock %.0f MHz" % sm_mhz,
                      "flops_per_path_step": FLOPS_PER_PATH_STEP, "path_kernel_ms": path_ms,
-                     "issue_note": "instruction-issue bound: 342 instructions per path-step at IPC 2.86 "
+                     "issue_note": "instruction-issue bound: 332 instructions per path-step at IPC 2.83 "
                                    "of 4 (0.71 of the issue rate; profiles/k_paths_d10_dense_n800.md)"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

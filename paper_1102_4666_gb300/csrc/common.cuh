@@ -67,15 +67,16 @@ struct Math<float> {
     const float u0 = fmaf(__uint2float_rn(w0), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     float lg;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(u0));
-    // sqrt(r2) as r2 * rsqrt(r2) (r2 >= 1e-30 keeps rsqrt finite)
-    const float r2 = fmaxf(lg * k, 1e-30f);
-    float rs, s, c;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r2));
-    const float rad = r2 * rs;
+    // radius: r2 = lg * k >= 0 (lg <= 0, k < 0), one approximate square
+    // root (sqrt(0) = 0 at u0 = 1: no clamp needed)
+    const float r2 = lg * k;
+    float rad, s, c;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rad) : "f"(r2));
     // angle 2 pi u1 - pi in (-pi, pi], straight from w1; cos/sin flip sign.
-    // The .ftz forms: no operand here is subnormal (r2 >= 1e-30, |angle| is
-    // 0 or above 1e-9), so flushing changes no result and saves the
-    // subnormal handling of the non-ftz forms.
+    // The .ftz forms: no operand here is subnormal (u0 >= 2^-33; r2 is 0 or
+    // above 1e-20 for any step h >= 1e-10; |angle| is 0 or above 1e-9), so
+    // flushing changes no result and saves the subnormal handling of the
+    // non-ftz forms.
     const float ang = fmaf(__uint2float_rn(w1), 1.4629180792671596e-09f, -3.1415926528f);
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(ang));
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(ang));
