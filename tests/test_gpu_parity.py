@@ -217,6 +217,33 @@ def test_teacher_forced_iteration_mixed(G, name, ev):
     assert np.max(np.abs(dg - do)) <= 1e-4 * max(np.max(np.abs(do)), 1e-2)
 
 
+# The path kernels are instantiated per dimension d; the cases above reach
+# d = 1, 2, 3, 5 and 10.  These reach the rest: d = 4 and 8 (one Euler step
+# per group of Philox blocks), 6 (two steps per group) and 7 and 9 (four),
+# with a degree-2 basis (dense degree-3 loops in FP32, tables in FP64) and a
+# degree-4 one (dense degree-4 loops at d = 4, the prefix-tree recursion at
+# d >= 6 in FP32; tables in FP64), n just above 2 p.
+DIM_CASES = [(d, eta, prec) for d in (4, 6, 7, 8, 9) for eta in (2, 4) for prec in ("fp64", "mixed")]
+
+
+@pytest.mark.parametrize("d,eta,prec", DIM_CASES)
+def test_teacher_forced_iteration_every_dimension(G, d, eta, prec):
+    p = workloads.basis_size(d, eta)
+    base = workloads.config("c3")
+    cfg = workloads.make(d=d, T=base["T"], r=base["r"], K=base["K"], S0=100.0, vol=base["vol"],
+                         rho=base["rho"], lam=base["lambda"], n=2 * p + 9, M=5 if eta == 4 else 37,
+                         N=3 if eta == 4 else 6, eta=eta, K_it=1, seed=40 + d)
+    nu = O.multi_index_set(d + 1, eta)
+    a0 = _alpha(cfg, nu)
+    s = solver(G, cfg, prec)
+    t, x, c, a1 = s.iterate(1, a0)
+    s.close()
+    it = O.iteration(cfg, nu, a0, 1, nthreads=NTH)
+    sc = _scale(cfg, nu, a0, t, x)
+    tol = 1e-9 if prec == "fp64" else MIXED_C_TOL
+    assert np.max(np.abs(c - it["c"])) < tol * sc
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_refit_solves_the_normal_equations(G, prec):
     """alpha^{k+1} - alpha^k is the least-squares fit of the GPU's own c on
