@@ -81,3 +81,46 @@ def test_paper_timing_workloads_follow_the_captions():
         assert t8 > tbest and procs in (64, 256)
     # the basis has d' = d + 1 variates: 35 functions at d = 3, 120 at d = 6
     assert workloads.basis_size(3, 3) == 35 and workloads.basis_size(6, 3) == 120
+
+
+def test_autotune_keeps_the_fastest_shape_and_skips_failing_ones(tmp_path, monkeypatch):
+    """tune() with the library's Solver replaced by a stand-in that reports
+    fixed path-kernel times: it probes a one-iteration problem, keeps the
+    fastest launch shape, skips shapes whose launch fails and writes the
+    problem class's entry to the cache; with every shape failing it returns
+    None and writes nothing."""
+    import paper_1102_4666_gb300 as G
+    from paper_1102_4666_gb300 import autotune
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("BSDE_TUNE_CACHE", str(path))
+    times = {(128, 4): 5.0, (256, 2): 3.0, (64, 8): 4.0}
+    probes = []
+
+    class Report:
+        def __init__(self, ms):
+            self.ms_paths = ms
+
+    class StandIn:
+        def __init__(self, cfg, precision="mixed"):
+            probes.append((cfg["K_it"], cfg["n"], precision))
+
+        def solve(self, use_graph=1, timing=0, paths_tpb=0, paths_ppt=0):
+            if (paths_tpb, paths_ppt) not in times:
+                raise RuntimeError("launch failed")
+            return Report(times[(paths_tpb, paths_ppt)])
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(G, "Solver", StandIn)
+    cfg = workloads.config("c3")
+    best = autotune.tune(cfg, "mixed", candidates=[(128, 4), (256, 2), (32, 32), (64, 8)], n_points=300)
+    assert best == (256, 2)
+    assert probes == [(1, 300, "mixed")]
+    assert autotune.lookup(cfg, "mixed") == (256, 2)
+    entry = json.loads(path.read_text())[autotune.key(cfg, "mixed")]
+    assert entry["ms_paths"] == 3.0 and set(entry["candidates"]) == {"128x4", "256x2", "64x8"}
+
+    path.unlink()
+    assert autotune.tune(cfg, "mixed", candidates=[(32, 32)]) is None
+    assert not path.exists()
