@@ -1,6 +1,7 @@
 """Host-side logic that needs no GPU: the autotuner's problem-class key and
 JSON cache, the seeded request mix of the serving benchmark, and the
-benchmark's arrival stream and weak-scaling arithmetic."""
+benchmark's arrival stream and weak-scaling arithmetic, the tuner's choice
+of a launch shape and the timing-table workloads."""
 import json
 import math
 
