@@ -109,7 +109,9 @@ BSDE_API const char* bsde_last_error(const bsde_ctx* ctx);
 /* Volatility and correlation of the model eq. eq4 (Section 5.1) with the
  * correlated Brownian motion of Section 6.2 (C = L L^*). */
 typedef struct {
-  int d;               /* number of assets, 1..BSDE_MAX_D                    */
+  int d;               /* number of assets, 1..BSDE_MAX_D; the path kernels  */
+                       /* are compiled for d = 1..10 (bsde_solve and        */
+                       /* bsde_iterate return BSDE_ERR_INVALID_ARG above)    */
   int kind;            /* BSDE_VOL_*                                          */
   const double* a;     /* d values a_j (NULL: a_scalar for every asset)      */
   double a_scalar;
