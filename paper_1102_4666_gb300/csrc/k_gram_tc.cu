@@ -11,9 +11,16 @@
 //   warp 0 / lane 0 : TMA producer (cp.async.bulk.tensor, 128B swizzle)
 //   warp 1 / lane 0 : MMA issuer (tcgen05.mma.cta_group::1.kind::tf32)
 //   warps 0-3       : epilogue, tcgen05.ld of the 128x128 FP32 accumulator
-// A 3-stage mbarrier ring overlaps loads and MMAs.  Every wait is bounded:
-// on expiry the kernel sets ST_TIMEOUT, stops issuing work, waits (bounded)
-// for what it already issued, frees its tensor memory and returns.
+// A 3-stage mbarrier ring overlaps loads and MMAs.  Every wait is bounded.
+// A wait for work that may never be issued (the producer waiting for a stage
+// the MMA issuer has not released, the issuer waiting for loads the producer
+// has not started) gives up after WAIT_LIMIT polls: the kernel then sets
+// ST_TIMEOUT and stops issuing.  Before it reads or frees its tensor memory
+// and before it exits, the CTA waits for everything it did issue (TMA loads
+// into its shared memory, committed MMAs into its tensor memory).  Issued
+// work completes without any further action of the CTA, so those drain
+// waits end; their bound (DRAIN_LIMIT polls, many seconds) only keeps every
+// loop finite.  If even a drain wait gave up, the accumulator is not read.
 // The FP32 partial tiles are summed in FP64 in split order by a second
 // kernel, so the result is deterministic.
 #include <cuda.h>
@@ -27,7 +34,8 @@ constexpr int KBLK = 32;        // tf32 elements per 128-byte swizzle row
 constexpr int STAGES = 3;
 constexpr int TILE_BYTES = TILE * KBLK * 4;  // 16 KB
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;  // Ahi, Alo, Bhi, Blo
-constexpr uint32_t WAIT_LIMIT = 1u << 26;    // spins before giving up
+constexpr uint32_t WAIT_LIMIT = 1u << 26;    // polls before giving up on unissued work
+constexpr uint32_t DRAIN_LIMIT = 1u << 30;   // polls of a wait for issued work
 
 struct GramArgs {
   int ntile_side;  // p_pad / 128
@@ -51,8 +59,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 }
 
 // bounded wait on the phase with the given parity; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          uint32_t limit = WAIT_LIMIT) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -114,7 +123,8 @@ __global__ void __launch_bounds__(128, 1)
   unsigned char* stage_mem = base;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
-  __shared__ int s_fail, s_issued, s_consumed;
+  __shared__ int s_fail, s_issued, s_consumed, s_acc_ok;
+  volatile int* fail_flag = &s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // tile (I <= J) and split
@@ -161,11 +171,11 @@ __global__ void __launch_bounds__(128, 1)
       if (it >= STAGES) {
         if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((it / STAGES) - 1) & 1))) {
           atomicOr(ga.status, ST_TIMEOUT);
-          s_fail = 1;
+          *fail_flag = 1;
           break;
         }
       }
-      if (s_fail) break;
+      if (*fail_flag) break;
       const uint32_t dst = smem_u32(stage_mem + s * STAGE_BYTES);
       const int kx = (kb0 + it) * KBLK;
       mbar_expect_tx(bar_full + 8 * s, STAGE_BYTES);
@@ -182,7 +192,7 @@ __global__ void __launch_bounds__(128, 1)
       const int s = it % STAGES;
       if (!mbar_wait(bar_full + 8 * s, (uint32_t)((it / STAGES) & 1))) {
         atomicOr(ga.status, ST_TIMEOUT);
-        s_fail = 1;
+        *fail_flag = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -200,24 +210,36 @@ __global__ void __launch_bounds__(128, 1)
       mma_commit(bar_empty + 8 * s);  // stage free once these MMAs complete
       s_consumed = it + 1;
     }
-    mma_commit(bar_acc);  // accumulator ready (or nothing issued)
+    // always issued: arrives once every MMA issued above has completed
+    // (at once when none was issued)
+    mma_commit(bar_acc);
   }
   __syncthreads();
-  // failure path only: wait (bounded) for loads issued but never consumed
   if (tid == 0) {
+    bool ok = true;
+    // failure path only: drain the loads issued but never consumed
     for (int it = s_consumed; it < s_issued; ++it)
-      if (!mbar_wait(bar_full + 8 * (it % STAGES), (uint32_t)((it / STAGES) & 1))) break;
+      ok = mbar_wait(bar_full + 8 * (it % STAGES), (uint32_t)((it / STAGES) & 1), DRAIN_LIMIT) && ok;
+    // drain the committed MMAs: after this the accumulator is final
+    ok = mbar_wait(bar_acc, 0, DRAIN_LIMIT) && ok;
+    if (!ok) atomicOr(ga.status, ST_TIMEOUT);
+    s_acc_ok = ok && !*fail_flag;
   }
-
-  // epilogue: every warp waits for the accumulator, then reads its 32 lanes
-  const bool ok = mbar_wait(bar_acc, 0);
-  if (!ok && lane == 0) atomicOr(ga.status, ST_TIMEOUT);
+  __syncthreads();
+  // CTA-uniform: tcgen05.ld is a warp-collective instruction
+  const bool ok = s_acc_ok != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int row = warp * 32 + lane;
   float* dst = ga.part + (((size_t)tile * ga.splits + split) * TILE + row) * TILE;
 #pragma unroll
   for (int cb = 0; cb < TILE / 32; ++cb) {
     uint32_t r[32];
+    if (!(ok && nk > 0)) {
+      float4* d4 = reinterpret_cast<float4*>(dst + cb * 32);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) d4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32);
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
@@ -232,14 +254,9 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     float4* d4 = reinterpret_cast<float4*>(dst + cb * 32);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      float4 v;
-      v.x = (ok && nk > 0) ? __uint_as_float(r[4 * q + 0]) : 0.0f;
-      v.y = (ok && nk > 0) ? __uint_as_float(r[4 * q + 1]) : 0.0f;
-      v.z = (ok && nk > 0) ? __uint_as_float(r[4 * q + 2]) : 0.0f;
-      v.w = (ok && nk > 0) ? __uint_as_float(r[4 * q + 3]) : 0.0f;
-      d4[q] = v;
-    }
+    for (int q = 0; q < 8; ++q)
+      d4[q] = make_float4(__uint_as_float(r[4 * q + 0]), __uint_as_float(r[4 * q + 1]),
+                          __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -303,25 +320,22 @@ bool make_map(CUtensorMap* map, const float* base, int n_pad, int p_pad) {
 
 }  // namespace
 
-// number of K splits: fill about one wave of 148 CTAs
-int gram_tc_splits(const ProblemDev& P) {
-  const int side = P.p_pad / TILE;
+// number of K splits: `want` when positive (at most one per K-block of 32
+// points), otherwise enough to fill about one wave of the device's SMs
+int gram_tc_splits(int p_pad, int n_pad, int want) {
+  const int side = p_pad / TILE;
   const int tiles = side * (side + 1) / 2;
-  const int kblocks = P.n_pad / KBLK;
-  int s = 148 / tiles;
+  const int kblocks = n_pad / KBLK;
+  int s = want > 0 ? want : device_sm_count() / tiles;
   if (s < 1) s = 1;
   if (s > kblocks) s = kblocks;
   return s;
 }
 
-size_t gram_tc_part_bytes(int p_pad, int n_pad) {
+size_t gram_tc_part_bytes(int p_pad, int n_pad, int splits) {
   const int side = p_pad / TILE;
   const int tiles = side * (side + 1) / 2;
-  const int kblocks = n_pad / KBLK;
-  int s = 148 / tiles;
-  if (s < 1) s = 1;
-  if (s > kblocks) s = kblocks;
-  return (size_t)tiles * s * TILE * TILE * sizeof(float);
+  return (size_t)tiles * splits * TILE * TILE * sizeof(float);
 }
 
 cudaError_t launch_gram_tc(const ProblemDev& P, cudaStream_t st) {
@@ -332,7 +346,7 @@ cudaError_t launch_gram_tc(const ProblemDev& P, cudaStream_t st) {
     return cudaErrorInvalidValue;
   GramArgs ga;
   ga.ntile_side = P.p_pad / TILE;
-  ga.splits = gram_tc_splits(P);
+  ga.splits = P.gram_splits > 0 ? P.gram_splits : gram_tc_splits(P.p_pad, P.n_pad, 0);
   ga.kblocks = P.n_pad / KBLK;
   ga.part = P.gram_part;
   ga.status = P.status;
