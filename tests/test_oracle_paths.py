@@ -63,6 +63,17 @@ def test_payoff_values():
     assert L.orc_payoff(m, O._dptr(x)) == 0.0
     x = np.log(np.array([50.0, 60.0, 70.0, 80.0, 90.0]))
     assert L.orc_payoff(m, O._dptr(x)) == pytest.approx(30.0, rel=1e-13)
+    # the call (eq. call_payoff): (sum_j w_j S_j - K)^+, zero below the strike
+    call = workloads.config("c3", payoff="call")
+    mc = O.model(call)
+    assert L.orc_payoff(mc, O._dptr(x)) == 0.0
+    x = np.log(np.array([110.0, 120.0, 130.0, 140.0, 150.0]))
+    assert L.orc_payoff(mc, O._dptr(x)) == pytest.approx(30.0, rel=1e-13)
+    assert L.orc_payoff(m, O._dptr(x)) == 0.0
+    # unequal weights enter as the basket sum_j w_j S_j
+    w = workloads.config("c3", payoff="call", weights=[0.5, 0.2, 0.1, 0.1, 0.1])
+    mw = O.model(w)
+    assert L.orc_payoff(mw, O._dptr(x)) == pytest.approx(0.5 * 110 + 24 + 13 + 14 + 15 - 100.0, rel=1e-13)
 
 
 def test_gbm_log_euler_is_exact_in_law():
@@ -99,14 +110,23 @@ def _undiscounted_put(S, K, r, sig, tau):
     return CF.bs_put(S, K, r, sig, tau) * math.exp(r * tau)
 
 
-def test_first_correction_is_expected_payoff():
-    """u^0 = 0, omega = 0: c^0(t,x) = E[Phi(X_T)] = e^{r(T-t)} BS_put."""
-    cfg = gbm_cfg()
+def _undiscounted_call(S, K, r, sig, tau):
+    if tau <= 0:
+        return max(S - K, 0.0)
+    return CF.bs_call(S, K, r, sig, tau) * math.exp(r * tau)
+
+
+@pytest.mark.parametrize("payoff", ["put", "call"])
+def test_first_correction_is_expected_payoff(payoff):
+    """u^0 = 0, omega = 0: c^0(t,x) = E[Phi(X_T)], that is e^{r(T-t)} BS_put
+    for the put and e^{r(T-t)} BS_call for the call (eq. call_payoff)."""
+    cfg = gbm_cfg(payoff=payoff)
     nu = O.multi_index_set(2, 2)
     alpha = np.zeros(len(nu))
+    expect = _undiscounted_put if payoff == "put" else _undiscounted_call
     for (t0, S) in [(0.0, 100.0), (0.5, 80.0), (0.9, 115.0)]:
         a = O.samples(cfg, nu, alpha, t0, np.array([math.log(S)]), 0, 0)
-        ref = _undiscounted_put(S, 100.0, 0.05, 0.25, 1.0 - t0)
+        ref = expect(S, 100.0, 0.05, 0.25, 1.0 - t0)
         se = a.std(ddof=1) / math.sqrt(len(a))
         assert abs(a.mean() - ref) < 4 * se
 
@@ -185,6 +205,50 @@ def test_penalty_term_of_the_driver():
     expect = _undiscounted_put(S, 100.0, 0.0, 0.25, 1 - t0) - c0 + lam * integral
     se = a.std(ddof=1) / math.sqrt(len(a))
     assert abs(a.mean() - expect) < 4 * se
+
+
+@pytest.mark.parametrize("payoff", ["put", "call"])
+@pytest.mark.parametrize("obstacle", ["payoff", "raw"])
+def test_penalty_obstacle_forms_separate(payoff, obstacle):
+    """The two obstacles of the penalty (eq. bsde-penal-2 and the literal
+    form of the d = 1 American configuration) with a negative constant
+    u^k = c0 < 0, r = 0, where they differ:
+      payoff form  lambda (Phi(X) - c0)^+  = lambda (Phi(X) + |c0|), so the
+                   time integral is lambda int (E[Phi(X_s)] + |c0|) ds;
+      raw form     lambda (I(X) - c0)^+ with I = K - S (put) or S - K (call),
+                   a put of strike K + |c0| or a call of strike K - |c0|.
+    Each expectation is a Black-Scholes price (r = 0), the integral by
+    Gauss-Legendre.  A sign or positive-part slip in either branch moves the
+    mean by many standard errors."""
+    lam, c0 = 3.0, -4.0
+    cfg = gbm_cfg(r=0.0, lam=lam, M=20000, payoff=payoff, obstacle=obstacle)
+    nu = O.multi_index_set(2, 2)
+    alpha = np.zeros(len(nu)); alpha[0] = c0
+    t0, S = 0.4, 97.0 if payoff == "put" else 103.0
+    a = O.samples(cfg, nu, alpha, t0, np.array([math.log(S)]), 0, 3)
+    price = _undiscounted_put if payoff == "put" else _undiscounted_call
+    gl_x, gl_w = np.polynomial.legendre.leggauss(40)
+    integral = 0.0
+    for x, w in zip(gl_x, gl_w):
+        tau = (1 - t0) * (x + 1) / 2
+        if obstacle == "payoff":
+            inner = price(S, 100.0, 0.0, 0.25, tau) - c0
+        else:
+            inner = price(S, 100.0 - c0 if payoff == "put" else 100.0 + c0, 0.0, 0.25, tau)
+        integral += w * (1 - t0) / 2 * inner
+    expect = price(S, 100.0, 0.0, 0.25, 1 - t0) - c0 + lam * integral
+    se = a.std(ddof=1) / math.sqrt(len(a))
+    assert abs(a.mean() - expect) < 4 * se
+    # the other form's expectation is far outside the Monte Carlo error
+    other = 0.0
+    for x, w in zip(gl_x, gl_w):
+        tau = (1 - t0) * (x + 1) / 2
+        if obstacle == "raw":
+            inner = price(S, 100.0, 0.0, 0.25, tau) - c0
+        else:
+            inner = price(S, 100.0 - c0 if payoff == "put" else 100.0 + c0, 0.0, 0.25, tau)
+        other += w * (1 - t0) / 2 * inner
+    assert abs(lam * (other - integral)) > 10 * se
 
 
 def test_correction_is_the_mean_of_the_samples():
