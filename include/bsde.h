@@ -188,6 +188,11 @@ typedef struct {
                        truncation at 1e-13 |R_00| on the design matrix (the
                        role of LAPACK dgelsy in Section 3.2.2; slower, for
                        ill-conditioned or rank-deficient bases)        */
+  int gram_splits;  /* slices of the point dimension of the tensor-core Gram
+                       matrix (BSDE_PREC_MIXED; each slice accumulates in
+                       FP32, the slices are summed in FP64): 0 automatic
+                       (one wave of the device's multiprocessors), else
+                       that many, at most one per 32 points; 0..4096    */
 } bsde_solve_params;
 
 typedef struct {
@@ -231,6 +236,20 @@ BSDE_API int bsde_solve(bsde_ctx* ctx, const bsde_solve_params* params, bsde_rep
  * The context's coefficients become alpha^{k+1}. */
 BSDE_API int bsde_iterate(bsde_ctx* ctx, const bsde_solve_params* params, int k, const double* alpha_in,
                  double* t_out, double* x_out, double* c_out, double* alpha_out);
+
+/* The Gram matrix A = sum_i B(t_i, x_i) B(t_i, x_i)^T of the normal
+ * equations (eq. alphasys, Section 3.2.2) at the n points of iteration k,
+ * B_l the basis functions in the order of bsde_basis_indices: A_out
+ * receives p x p FP64 values, row-major (cap: its capacity in values,
+ * at least p * p).  It is the matrix that the refit of iteration k in a
+ * solve with the same parameters factorises: with BSDE_PREC_MIXED the 3xTF32
+ * tensor-core product (each basis value split into two TF32 parts, FP32
+ * accumulation within each of gram_splits slices of the points, the slices
+ * summed in FP64), with BSDE_PREC_FP64 the FP64 product.  Needs set_model and
+ * set_grid; the coefficients of the context are left unchanged.  Errors as
+ * bsde_solve, and BSDE_ERR_INVALID_ARG when cap < p * p. */
+BSDE_API int bsde_gram_matrix(bsde_ctx* ctx, const bsde_solve_params* params, int k, double* A_out,
+                              int cap);
 
 /* Basis size p of the current solve parameters, and the multi-indices in
  * the library's order (p x (d+1) ints, graded, lexicographically descending

@@ -70,7 +70,8 @@ class bsde_solve_params(ctypes.Structure):
                 ("K_it", ctypes.c_int), ("seed", ctypes.c_uint64), ("k_start", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("use_graph", ctypes.c_int), ("timing", ctypes.c_int),
                 ("allow_underdetermined", ctypes.c_int), ("eval_mode", ctypes.c_int),
-                ("paths_tpb", ctypes.c_int), ("paths_ppt", ctypes.c_int), ("ls_mode", ctypes.c_int)]
+                ("paths_tpb", ctypes.c_int), ("paths_ppt", ctypes.c_int), ("ls_mode", ctypes.c_int),
+                ("gram_splits", ctypes.c_int)]
 
 
 class bsde_report(ctypes.Structure):
@@ -124,6 +125,8 @@ _SIGNATURES = {
                                   ctypes.POINTER(bsde_report)]),
     "bsde_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bsde_solve_params), ctypes.c_int, _dptr,
                                     _dptr, _dptr, _dptr, _dptr]),
+    "bsde_gram_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bsde_solve_params), ctypes.c_int,
+                                        _dptr, ctypes.c_int]),
     "bsde_basis_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_int)]),
     "bsde_basis_indices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -237,7 +240,7 @@ def model_structs(cfg):
 
 
 def solve_params(cfg, seed=None, K_it=None, k_start=0, refine_steps=-1, use_graph=1, timing=0,
-                 allow_underdetermined=0, eval_mode=0, paths_tpb=0, paths_ppt=0, ls_mode=0):
+                 allow_underdetermined=0, eval_mode=0, paths_tpb=0, paths_ppt=0, ls_mode=0, gram_splits=0):
     p = bsde_solve_params()
     p.M, p.N_steps, p.eta, p.q = cfg["M"], cfg["N"], cfg["eta"], cfg.get("q", 1.0)
     p.K_it = cfg["K_it"] if K_it is None else K_it
@@ -247,6 +250,7 @@ def solve_params(cfg, seed=None, K_it=None, k_start=0, refine_steps=-1, use_grap
     p.eval_mode = eval_mode
     p.paths_tpb, p.paths_ppt = paths_tpb, paths_ppt
     p.ls_mode = ls_mode
+    p.gram_splits = gram_splits
     return p
 
 
@@ -293,7 +297,7 @@ class Solver:
     """One context of the C ABI set up from a workload dictionary."""
 
     def __init__(self, cfg, precision="mixed", device=0, stream=None, torch_memory=True, mem_budget=0,
-                 launch_shape=None):
+                 launch_shape=None, allocator=None):
         self.cfg = cfg
         # (threads per CTA, paths per thread) of the path kernel, e.g. from
         # autotune.lookup()/tune(); None leaves the library's choice
@@ -301,7 +305,13 @@ class Solver:
         o = bsde_create_opts()
         o.device = device
         o.stream = stream
-        if torch_memory:
+        if allocator is not None:
+            # an object with alloc(nbytes, stream) -> device address or None
+            # and free(ptr, stream); the callbacks live as long as the Solver
+            self._hooks = (alloc_fn(lambda nb, st, u: allocator.alloc(nb, st)),
+                           free_fn(lambda ptr, st, u: allocator.free(ptr, st)))
+            o.alloc, o.free = self._hooks
+        elif torch_memory:
             a, f = torch_allocator()
             o.alloc, o.free = a, f
         o.mem_budget = mem_budget
@@ -356,6 +366,16 @@ class Solver:
         if check:
             self._check(rc)
         return t, x.reshape(d, n), c, an
+
+    def gram(self, k, **kw):
+        """The Gram matrix B^T B of iteration k's points (p x p), as the
+        refit of a solve with these parameters would factorise it."""
+        import numpy as np
+        p = solve_params(self.cfg, **self._shape(kw))
+        P = self.basis_size(p.eta, p.q)
+        A = np.zeros((P, P))
+        self._check(lib().bsde_gram_matrix(self.h, ctypes.byref(p), k, A.ctypes.data_as(_dptr), P * P))
+        return A
 
     def basis_size(self, eta=None, q=None):
         eta = self.cfg["eta"] if eta is None else eta

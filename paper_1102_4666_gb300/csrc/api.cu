@@ -196,6 +196,35 @@ int bsde_iterate(bsde_ctx* c, const bsde_solve_params* prm, int k, const double*
   })
 }
 
+int bsde_gram_matrix(bsde_ctx* c, const bsde_solve_params* prm, int k, double* A_out, int cap) {
+  if (!c) return BSDE_ERR_INVALID_ARG;
+  if (!prm || !A_out || k < 0 || k >= (1 << 24))
+    return fail(c, BSDE_ERR_INVALID_ARG, "gram: bad arguments");
+  API_GUARD(c, {
+    if (!set_device(c)) return fail(c, BSDE_ERR_CUDA, "gram: cudaSetDevice failed");
+    bsde_solve_params p1 = *prm;
+    p1.K_it = 1;
+    p1.k_start = k;
+    Problem& P = c->prob;
+    int rc = P.prepare(p1, c->al, c->budget, c->stream);
+    if (rc != BSDE_OK) return fail(c, rc, P.err);
+    const int p = P.shape.p;
+    if ((long long)cap < (long long)p * p)
+      return fail(c, BSDE_ERR_INVALID_ARG, "gram: capacity below p * p");
+    rc = P.enqueue_gram(k, c->stream);
+    if (rc != BSDE_OK) return fail(c, rc, P.err);
+    int status = 0;
+    cudaError_t e =
+        cudaMemcpyAsync(A_out, P.dev.A, (size_t)p * p * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&status, P.dev.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, BSDE_ERR_CUDA, std::string("gram: ") + cudaGetErrorString(e));
+    if (status & ST_TIMEOUT) return fail(c, BSDE_ERR_TIMEOUT, "gram: a bounded device wait gave up");
+    return BSDE_OK;
+  })
+}
+
 int bsde_basis_size(int d, int eta, double q, int* p_out) {
   if (d < 1 || d > BSDE_MAX_D || eta < 0 || eta > 15 || !(q > 0.0) || q > 1.0 || !p_out)
     return BSDE_ERR_INVALID_ARG;

@@ -143,6 +143,7 @@ struct GridHost {
 // Device pointers of one resident problem (one context or one served request)
 struct ProblemDev {
   int n = 0, n_pad = 0, p = 0, p_pad = 0, eta = 0, chunks = 0;
+  int gram_splits = 0;        // K splits of the tensor-core Gram (mixed)
   double* t = nullptr;        // [n]
   double* x = nullptr;        // [d][n]
   double* B = nullptr;        // [p][n_pad] FP64 basis matrix, point index fastest
@@ -211,7 +212,12 @@ cudaError_t launch_paths(const ModelHost& m, const GridHost& g, const ProblemDev
 void launch_reduce_c(const ProblemDev& P, int M, cudaStream_t st);
 void launch_gram_f64(const ProblemDev& P, cudaStream_t st);
 cudaError_t launch_gram_tc(const ProblemDev& P, cudaStream_t st);
-int gram_tc_splits(const ProblemDev& P);
+// K splits of the tensor-core Gram (want > 0: that many, capped by the
+// K-blocks; 0: one wave of the device's SMs) and the bytes of its partial tiles
+int gram_tc_splits(int p_pad, int n_pad, int want);
+size_t gram_tc_part_bytes(int p_pad, int n_pad, int splits);
+// multiprocessor count of the current device (cached per device)
+int device_sm_count();
 void launch_rhs(const ProblemDev& P, cudaStream_t st);
 // batched over nb Gram matrices (P.A, P.dinv, P.diag0, P.Ainv hold nb of them)
 void launch_cholesky(const ProblemDev& P, int nb, cudaStream_t st);

@@ -67,6 +67,26 @@ void Allocator::put(void* p, cudaStream_t st) {
   }
 }
 
+int device_sm_count() {
+  static std::mutex mu;
+  static int cache[POOL_DEVICES] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= POOL_DEVICES) {
+    cudaGetLastError();
+    return 1;
+  }
+  std::lock_guard<std::mutex> g(mu);
+  if (cache[dev] == 0) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      return 1;
+    }
+    cache[dev] = sms;
+  }
+  return cache[dev];
+}
+
 static bool is_fin(double v) { return std::isfinite(v); }
 
 // Cholesky-Banachiewicz of the d x d correlation (C = L L^*, Section 6.2)
@@ -213,7 +233,7 @@ size_t Problem::fact_block_bytes(int p, int nfact) {
 }
 
 size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int tpb, int ppt, int pm,
-                               int conv_nnz, bool qr, int nfact) {
+                               int conv_nnz, bool qr, int nfact, int splits) {
   (void)N;
   const int n_pad = (n + 31) / 32 * 32;
   const int p_pad = (p + 127) / 128 * 128;
@@ -226,11 +246,7 @@ size_t Problem::estimate_bytes(int d, int n, int p, int M, int N, bool mx, int t
   if (mx) {
     add((size_t)p_pad * n_pad * 4);
     add((size_t)p_pad * n_pad * 4);
-    const int side = p_pad / 128, tiles = side * (side + 1) / 2;
-    int s = 148 / tiles;
-    if (s < 1) s = 1;
-    if (s > n_pad / 32) s = n_pad / 32;
-    add((size_t)tiles * s * 128 * 128 * 4);
+    add(gram_tc_part_bytes(p_pad, n_pad, gram_tc_splits(p_pad, n_pad, splits)));
   }
   add((size_t)n * chunks * 8);
   add((size_t)n * 8);
@@ -376,10 +392,15 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     s.ppt = prm.paths_ppt;
   }
   s.chunks = (s.M + s.tpb * s.ppt - 1) / (s.tpb * s.ppt);
+  if (prm.gram_splits < 0 || prm.gram_splits > 4096) {
+    err = "solve: gram_splits must be in 0..4096";
+    return BSDE_ERR_INVALID_ARG;
+  }
+  s.splits = mixed ? gram_tc_splits(s.p_pad, s.n_pad, prm.gram_splits) : 0;
   const int nf = fact_group(p, prm.K_it, grid.resample != 0, s.qr);
   {
     const size_t total = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt, s.pm,
-                                        s.dense ? (int)conv_l.size() : 0, s.qr, nf);
+                                        s.dense ? (int)conv_l.size() : 0, s.qr, nf, s.splits);
     if (budget && total > budget) {
       std::ostringstream os;
       os << "solve: needs " << total << " bytes of device memory, budget " << budget;
@@ -389,13 +410,14 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   }
   if (!block || !(s == alloc_shape)) {
     const size_t need = estimate_bytes(d, n, p, s.M, s.N, mixed, s.tpb, s.ppt, s.pm,
-                                       s.dense ? (int)conv_l.size() : 0, s.qr, 0);
+                                       s.dense ? (int)conv_l.size() : 0, s.qr, 0, s.splits);
     destroy_graph();
     if (block) al.put(block, st);
     block = nullptr;
     block_bytes = 0;
     void* b = al.get(need, st);
     if (!b) {
+      release(al, st);  // a failed call leaves the context holding no device memory
       err = "solve: device allocation failed";
       return BSDE_ERR_NOMEM;
     }
@@ -425,11 +447,8 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     if (mixed) {
       P.Bhi = (float*)take((size_t)s.p_pad * s.n_pad * 4);
       P.Blo = (float*)take((size_t)s.p_pad * s.n_pad * 4);
-      const int side = s.p_pad / 128, tiles = side * (side + 1) / 2;
-      int sp = 148 / tiles;
-      if (sp < 1) sp = 1;
-      if (sp > s.n_pad / 32) sp = s.n_pad / 32;
-      P.gram_part = (float*)take((size_t)tiles * sp * 128 * 128 * 4);
+      P.gram_splits = s.splits;
+      P.gram_part = (float*)take(gram_tc_part_bytes(s.p_pad, s.n_pad, s.splits));
     }
     P.partial = (double*)take((size_t)n * s.chunks * 8);
     P.c = (double*)take((size_t)n * 8);
@@ -477,6 +496,7 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
       fact = al.get(fneed, st);
       fact_bytes = fact ? fneed : 0;
       if (!fact) {
+        release(al, st);
         err = "solve: device allocation failed (Gram factors)";
         return BSDE_ERR_NOMEM;
       }
@@ -554,6 +574,30 @@ int Problem::enqueue_factors(int k0, int nb, cudaStream_t st) {
   }
   launch_cholesky(dev, nb, st);
   launch_inverse(dev, nb, st);
+  return BSDE_OK;
+}
+
+int Problem::enqueue_gram(int k, cudaStream_t st) {
+  if (nfact < 1 || dev.A == nullptr) {
+    err = "gram: no factor block";
+    return BSDE_ERR_STATE;
+  }
+  launch_points(model, grid, dev, grid.resample ? (uint32_t)k : 0u, st);
+  launch_basis(model, grid, dev, mixed, st);
+  if (mixed) {
+    const cudaError_t e = launch_gram_tc(dev, st);
+    if (e != cudaSuccess) {
+      err = std::string("tensor-core Gram launch failed: ") + cudaGetErrorString(e);
+      return BSDE_ERR_CUDA;
+    }
+  } else {
+    launch_gram_f64(dev, st);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("gram: kernel launch failed: ") + cudaGetErrorString(e);
+    return BSDE_ERR_CUDA;
+  }
   return BSDE_OK;
 }
 
@@ -664,7 +708,8 @@ int Problem::start(const bsde_solve_params& prm, Allocator& al, size_t budget, c
     os << shape.d << ' ' << shape.n << ' ' << shape.p << ' ' << shape.M << ' ' << shape.N << ' '
        << prm.K_it << ' ' << prm.k_start << ' ' << prm.refine_steps << ' ' << prm.timing << ' '
        << mixed << ' ' << (void*)block << ' ' << prm.seed << ' ' << prm.eval_mode << ' '
-       << prm.paths_tpb << ' ' << prm.paths_ppt << ' ' << prm.ls_mode << ' ' << fact << ' ' << nfact;
+       << prm.paths_tpb << ' ' << prm.paths_ppt << ' ' << prm.ls_mode << ' ' << fact << ' ' << nfact
+       << ' ' << shape.splits;
     if (!gexec || os.str() != graph_key) {
       destroy_graph();
       cudaGraph_t graph = nullptr;

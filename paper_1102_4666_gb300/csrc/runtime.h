@@ -26,7 +26,7 @@ struct Shape {
   bool operator==(const Shape& o) const {
     return d == o.d && n == o.n && p == o.p && eta == o.eta && M == o.M && N == o.N &&
            tpb == o.tpb && ppt == o.ppt && mixed == o.mixed && dense == o.dense &&
-           dense4 == o.dense4 && tree == o.tree && pm == o.pm && qr == o.qr;
+           dense4 == o.dense4 && tree == o.tree && pm == o.pm && qr == o.qr && splits == o.splits;
   }
 };
 
@@ -61,6 +61,9 @@ class Problem {
   int solve(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st,
             bsde_report* rep);
   int enqueue_solve(const bsde_solve_params& prm, cudaStream_t st);  // after prepare
+  // points, basis matrix and Gram matrix of iteration k into factor slot 0
+  // (after prepare)
+  int enqueue_gram(int k, cudaStream_t st);
   // asynchronous halves of solve(): start() enqueues (graph or launches)
   // between events e0 and e1; complete() waits for e1 and builds the report
   int start(const bsde_solve_params& prm, Allocator& al, size_t budget, cudaStream_t st,
@@ -73,7 +76,8 @@ class Problem {
   void destroy_graph();  // after a model or grid change
   size_t bytes() const { return block_bytes + fact_bytes; }
   static size_t estimate_bytes(int d, int n, int p, int M, int N, bool mixed, int tpb, int ppt,
-                               int pm = 0, int conv_nnz = 0, bool qr = false, int nfact = 1);
+                               int pm = 0, int conv_nnz = 0, bool qr = false, int nfact = 1,
+                               int splits = 0);
   // Gram matrices factorised together ahead of their iterations: all K_it
   // of a solve while their factors and inverses fit in 256 MiB (one when
   // the points are not redrawn, none for the QR refit)

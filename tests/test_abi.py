@@ -49,7 +49,7 @@ int main(void) {
   P(bsde_sigma) O(bsde_sigma, div) O(bsde_sigma, rho)
   P(bsde_payoff) O(bsde_payoff, weights)
   P(bsde_penalty) O(bsde_penalty, obstacle)
-  P(bsde_solve_params) O(bsde_solve_params, seed) O(bsde_solve_params, allow_underdetermined) O(bsde_solve_params, eval_mode) O(bsde_solve_params, paths_ppt) O(bsde_solve_params, ls_mode)
+  P(bsde_solve_params) O(bsde_solve_params, seed) O(bsde_solve_params, allow_underdetermined) O(bsde_solve_params, eval_mode) O(bsde_solve_params, paths_ppt) O(bsde_solve_params, ls_mode) O(bsde_solve_params, gram_splits)
   P(bsde_report) O(bsde_report, ms_total) O(bsde_report, kernel_launches) O(bsde_report, resid_linf) O(bsde_report, rank)
   P(bsde_server_opts) O(bsde_server_opts, precision) O(bsde_server_opts, policy)
   P(bsde_request) O(bsde_request, params) O(bsde_request, hi) O(bsde_request, n)
