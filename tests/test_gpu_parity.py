@@ -139,6 +139,16 @@ CASES = {
     # cross terms of the per-thread table evaluation
     "d3_full_corr": ("c3", dict(d=3, n=90, M=130, N=9, eta=3,
                                 corr=[[1.0, 0.3, -0.1], [0.3, 1.0, 0.5], [-0.1, 0.5, 1.0]])),
+    # hyperbolic index sets (eq. hyper_set, q < 1): d = 10 degree 5 with
+    # q = 0.6 (p = 221, per-thread tables), d = 10 degree 4 with q = 0.7
+    # (p = 210, prefix-tree recursion over the kept monomials in FP32) and
+    # d = 5 degree 6 with q = 0.75 (p = 237, degree-6 prefix tree in FP32)
+    "d10_hyperbolic": ("c4", dict(n=460, M=24, N=5, eta=5, q=0.6)),
+    "d10_hyperbolic_deg4": ("c4", dict(n=430, M=16, N=4, eta=4, q=0.7)),
+    "d5_hyperbolic_deg6": ("c3", dict(n=480, M=24, N=5, eta=6, q=0.75)),
+    # a call with the raw obstacle of the penalty (both differ from the
+    # put with the payoff obstacle in the driver)
+    "d2_call_raw": ("c3", dict(d=2, n=64, M=90, N=6, eta=3, payoff="call", obstacle="raw")),
 }
 
 
@@ -163,13 +173,26 @@ def _alpha(cfg, nu, scale=2.0, seed=3):
     return a
 
 
+def _nu(cfg):
+    return O.multi_index_set(cfg["d"] + 1, cfg["eta"], cfg.get("q", 1.0))
+
+
+def _phi_scale(cfg):
+    """Size of the payoff (and of the obstacle in the penalty) by payoff kind:
+    a put (K - basket)^+ never exceeds K; a call (basket - K)^+ reaches
+    sum_j w_j e^{hi_j} - K at the top corner of the box.  The raw obstacle
+    K - basket (put) or basket - K (call) has the same upper end."""
+    if cfg["payoff"] == "put":
+        return cfg["K"]
+    return max(1.0, float(np.dot(cfg["weights"], np.exp(cfg["hi"][1:]))) - cfg["K"])
+
+
 def _scale(cfg, nu, alpha, t, x):
     """Scale of the integrand a_m = (T - t)(-r u + lambda (Phi - u)^+ + d_t u + L u)
     + Phi - u (eq. psiN with the driver of eq. bsde-penal-2): both u and the
     payoff Phi enter multiplied by up to 1 + lambda T."""
     u = O.basis_matrix(cfg, nu, t, x) @ alpha
-    phi_max = max(cfg["K"], float(np.dot(cfg["weights"], np.exp(cfg["hi"][1:]))))
-    return max(1.0, phi_max, np.max(np.abs(u))) * (1.0 + cfg["lambda"] * cfg["T"])
+    return max(1.0, _phi_scale(cfg), np.max(np.abs(u))) * (1.0 + cfg["lambda"] * cfg["T"])
 
 
 # (case, eval_mode): 0 automatic (dense monomial form for total degree <= 3,
@@ -188,7 +211,7 @@ EVAL_CASES = [(n, 0) for n in CASES] + [(n, 1) for n in CASES if _dense_applies(
 @pytest.mark.parametrize("name,ev", EVAL_CASES)
 def test_teacher_forced_iteration_fp64(G, name, ev):
     cfg = _case(name)
-    nu = O.multi_index_set(cfg["d"] + 1, cfg["eta"])
+    nu = _nu(cfg)
     a0 = _alpha(cfg, nu)
     s = solver(G, cfg, "fp64")
     t, x, c, a1 = s.iterate(2, a0, eval_mode=ev)
@@ -196,13 +219,15 @@ def test_teacher_forced_iteration_fp64(G, name, ev):
     it = O.iteration(cfg, nu, a0, 2, nthreads=NTH)
     sc = _scale(cfg, nu, a0, t, x)
     assert np.max(np.abs(c - it["c"])) < 1e-9 * sc
-    assert rel(a1 - a0, it["alpha"] - a0) < 1e-8
+    # the coefficients alpha^{k+1} to 1e-9 relative, and the increment too
+    assert rel(a1, it["alpha"]) < 1e-9
+    assert rel(a1 - a0, it["alpha"] - a0) < 1e-9
 
 
 @pytest.mark.parametrize("name,ev", EVAL_CASES)
 def test_teacher_forced_iteration_mixed(G, name, ev):
     cfg = _case(name)
-    nu = O.multi_index_set(cfg["d"] + 1, cfg["eta"])
+    nu = _nu(cfg)
     a0 = _alpha(cfg, nu)
     s = solver(G, cfg, "mixed")
     t, x, c, a1 = s.iterate(2, a0, eval_mode=ev)
