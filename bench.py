@@ -29,22 +29,16 @@ METRIC = "path-steps/s incl. u^k,∇u^k,Lu^k eval at d=10 (vs FP64 plain); p50/p
 UNIT = "path-steps/s"
 CONFIG = "c4"
 
-# Algorithmic FP32 work of one Euler path-step at d = 10 (an FMA counts 2),
-# for the plain formulation of the step, rounded: correlation L Z as a
-# triangular product (55 multiply-adds, ~100), local volatility 10 x 8,
-# drift and update 10 x 7, Box-Muller 5 pairs x 10 -> ~300.  The kernel executes fewer FP32 operations than this
-# (prefix sums for the constant correlation, tabulated volatility
-# coefficients, one Box-Muller radius factor); the per-path evaluation of
-# u^k and its derivatives (~11k flops for p = 364, ~110 per step at N = 100)
-# is not counted.
-FLOPS_PER_PATH_STEP = 300.0
-SMS, FP32_LANES = 152, 128
-# DRAM bytes (read + write) of one path-kernel launch per point, from the ncu
-# capture summarised in profiles/k_paths_d10_dense_n800.md (n = 800 points:
-# 144.6 KB read, 0 B written: the partial sums stay in L2), scaled to a
+FP32_LANES = 128  # FP32 lanes per SM (sm_103a)
+# DRAM bytes (read + write) of one path-kernel launch per point, from an ncu
+# capture of the same kernel on the d = 10 workload with n = 800 points
+# (144.6 KB read, 0 B written: the partial sums stay in L2), scaled to a
 # launch over n points (the kernel reads the points and coefficients and
 # writes one partial sum per (point, chunk), both proportional to n).
 PATH_TRAFFIC_BYTES_PER_POINT = (144640.0 + 0.0) / 800.0
+# instruction issue of the same capture: warp instructions per path-step and
+# instructions issued per SM cycle (of 4)
+PATH_ISSUE = {"instructions_per_path_step": 331.9, "ipc": 2.83, "ipc_peak": 4.0}
 
 
 def env_rank():
@@ -479,9 +473,14 @@ def run_ours(args):
                          "path_steps_per_s": best.path_steps_per_s}
         paper[name] = row
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled clock
     launch_steps = cfg["n"] * cfg["M"] * cfg["N"]
-    achieved = FLOPS_PER_PATH_STEP * launch_steps / (path_ms * 1e-3) / 1e12 if path_ms > 0 else None
+    from paper_1102_4666_gb300 import flops as FL
+    fc = FL.per_path_step(cfg["d"], cfg["N"])
+    tf = (lambda f: f * launch_steps / (path_ms * 1e-3) / 1e12 if path_ms > 0 else None)
+    achieved = tf(fc["flops_with_eval"])
+    achieved_steps = tf(fc["flops_steps_only"])
     cpu = None
     if not args.no_cpu:
         # the GPU's corrections of the iteration the oracle times (same
@@ -510,10 +509,23 @@ def run_ours(args):
                      "traffic": (PATH_TRAFFIC_BYTES_PER_POINT * cfg["n"]
                                  if PATH_TRAFFIC_BYTES_PER_POINT else None),
                      "traffic_basis": "dram read+write per launch from the n=800 ncu capture, scaled by n",
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x sampled SM clock %.0f MHz" % sm_mhz,
-                     "flops_per_path_step": FLOPS_PER_PATH_STEP, "path_kernel_ms": path_ms,
-                     "issue_note": "instruction-issue bound: 332 instructions per path-step at IPC 2.83 "
-                                   "of 4 (0.71 of the issue rate; profiles/k_paths_d10_dense_n800.md)"},
+                     "sm_count": sms,
+                     "peak_basis": "%d SMs (device attribute) x 128 FP32 lanes x 2 flop x sampled SM clock "
+                                   "%.0f MHz" % (sms, sm_mhz),
+                     "flops_per_path_step": fc["flops_with_eval"],
+                     "flops_breakdown": {
+                         "euler_step": fc["step_flops"],
+                         "per_path_eval_u_grad_Lu": fc["eval_flops_per_path"],
+                         "per_path_bridge_payoff_driver": fc["other_flops_per_path"],
+                         "N_steps": cfg["N"],
+                         "basis": "FP32 operations of the kernel source (FMA = 2), "
+                                  "paper_1102_4666_gb300/flops.py; MUFU operations apart",
+                         "mufu_per_path_step": fc["mufu_per_step"]},
+                     "achieved_steps_only": achieved_steps,
+                     "frac_steps_only": (achieved_steps / peak) if achieved_steps else None,
+                     "path_kernel_ms": path_ms,
+                     "issue": dict(PATH_ISSUE, frac=PATH_ISSUE["ipc"] / PATH_ISSUE["ipc_peak"],
+                                   basis="ncu capture of this kernel (d = 10, n = 800)")},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
