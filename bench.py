@@ -9,7 +9,9 @@ Metric: path-steps/s = K_it n M N / time.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank solves its own independent problem (its
-own seed): weak scaling with no data-path collective.
+own seed): weak scaling with no data-path collective.  With --shard the ranks
+share one problem instead: each simulates a block of the points and the
+corrections are all-gathered once per iteration (strong scaling).
 """
 import argparse
 import json
@@ -366,11 +368,19 @@ def run_ours(args):
     import paper_1102_4666_gb300 as G
 
     cfg = workloads.config(CONFIG)
-    cfg["seed"] = rank_seed(cfg["seed"], rank)  # independent problem per rank
+    shard = args.shard and world > 1
+    if not shard:
+        cfg["seed"] = rank_seed(cfg["seed"], rank)  # independent problem per rank
     from paper_1102_4666_gb300 import autotune
     shape = autotune.lookup(cfg, "mixed") or autotune.tune(cfg, "mixed", repeats=3)
     stream = torch.cuda.Stream(device=dev)
     s = G.Solver(cfg, precision="mixed", device=local, stream=stream.cuda_stream, launch_shape=shape)
+    if shard:
+        # one problem, its points in blocks over the ranks, one all-gather of
+        # the corrections per iteration (strong scaling)
+        nb = (cfg["n"] + world - 1) // world
+        xbuf = torch.zeros(world * nb, dtype=torch.float64, device=dev)
+        s.set_shard(rank, world, xbuf, G.torch_distributed_exchange())
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def step(timing=1):
@@ -403,6 +413,8 @@ def run_ours(args):
     clk = clocks.stop()
     steps_per_solve = workloads.path_steps(cfg)
     value, ms = weak_scaling_value(ms, args.steps, steps_per_solve, device=dev)
+    if shard:  # every rank worked on the same problem
+        value /= world
     launches = sum(r.kernel_launches for r in reps)
     path_ms = sum(r.ms_paths for r in reps) / max(1, sum(r.path_launches for r in reps))
 
@@ -419,6 +431,8 @@ def run_ours(args):
         _ = (r.price, list(r.delta))
     e2e_s = time.perf_counter() - t0
     e2e_val, e2e_ms = weak_scaling_value(e2e_s * 1e3, args.steps, steps_per_solve, device=dev)
+    if shard:
+        e2e_val /= world
     p = 364
     h2d = p * 8 + p + cfg["d"] * 8 + 8 + 4   # basis tables, log S0, key, status reset
     d2h = (1 + 16 + 3 * 64) * 8 + 4          # report block and status word
@@ -496,12 +510,15 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "f32",
         "dtype_detail": "f32 paths and evaluation, f64 per-point sums, 3xTF32 Gram, f64 Cholesky/refit",
         "data": "synthetic",
         "config": {"workload": cfg["name"], "d": 10, "n": cfg["n"], "M": cfg["M"], "N": cfg["N"],
                    "eta": 3, "p": rep0.p, "K_it": cfg["K_it"], "precision": "mixed",
-                   "l2": "flushed between steps (256 MB write)", "graph": True,
+                   "l2": "flushed between steps (256 MB write)", "graph": not shard,
+                   "parallelism": ("points sharded over %d ranks, one all-gather of the corrections "
+                                   "per iteration" % world) if shard else
+                                  ("one independent problem per rank" if world > 1 else "one GPU"),
                    "paths_launch_shape": list(shape) if shape else None},
         "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,EV_DENSE3,CC,float,10>",
                      "achieved": achieved,
@@ -564,6 +581,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=100,
                     help="requests of the Poisson serving mix (0: skip; 2000: the full mix)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: shard the points of one problem over the ranks (strong "
+                         "scaling) instead of one independent problem per rank (weak scaling)")
     args = ap.parse_args()
     if args.case in ("profile", "profile_tree"):
         return run_profile_case(args)

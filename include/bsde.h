@@ -57,6 +57,7 @@ extern "C" {
 #define BSDE_ERR_NOT_PD -5      /* Gram matrix not positive definite      */
 #define BSDE_ERR_TIMEOUT -6     /* a bounded device wait gave up          */
 #define BSDE_ERR_CUDA -7        /* CUDA runtime error                     */
+#define BSDE_ERR_EXCHANGE -8    /* the exchange hook of a sharded solve failed */
 
 /* arithmetic of the path simulation and evaluation */
 #define BSDE_PREC_FP64 0  /* everything in FP64 ("plain" comparator)      */
@@ -250,6 +251,40 @@ BSDE_API int bsde_iterate(bsde_ctx* ctx, const bsde_solve_params* params, int k,
  * bsde_solve, and BSDE_ERR_INVALID_ARG when cap < p * p. */
 BSDE_API int bsde_gram_matrix(bsde_ctx* ctx, const bsde_solve_params* params, int k, double* A_out,
                               int cap);
+
+/* ------------------------------------------------------------------------
+ * Point sharding (Section 4.2: the loop over the points of an iteration is
+ * parallel, and the paper's master/slave scheme of Section 4.3 distributes
+ * it).  With nranks > 1, rank `rank` of a group of contexts (normally one
+ * process per GPU) runs the path kernel and the per-point reduction only on
+ * its block of points [i0, i1) = bsde_shard_block(n, rank, nranks): blocks
+ * of nb = ceil(n / nranks) consecutive points, the last one shorter.  Every
+ * rank draws all n points itself (they depend on (seed, k) only) and builds
+ * the basis matrix, the Gram matrices and their factors of all n points, so
+ * the only data that crosses ranks is the corrections c_i: once per
+ * iteration, after its block's c_i are written (stream-ordered) to
+ * c_dev[i0 .. i1), the library calls on the host
+ *     exchange(c_dev, nb, rank, nranks, stream, user)
+ * which must enqueue on `stream`, or make `stream` wait for, an operation
+ * after which c_dev[q nb .. q nb + nb) holds the block of every rank q
+ * (an all-gather of nb doubles per rank, e.g. ncclAllGather in place with
+ * sendbuff = c_dev + rank nb); it returns 0, or nonzero to make the solve
+ * fail with BSDE_ERR_EXCHANGE.  The refit then uses all n corrections
+ * exactly as the unsharded solve does: every rank ends with the same
+ * coefficients, equal bit for bit to those of the unsharded solve.
+ *   c_dev, c_len: device buffer of the caller (c_len doubles, at least
+ *   nranks * nb for the grid of the solve), read and written on the
+ *   context's stream; it must stay valid while the setting holds.
+ * nranks = 1 turns sharding off (c_dev and exchange may then be NULL).
+ * While sharded, solves run as direct launches (use_graph is ignored: the
+ * exchange is a host call in every iteration).  Errors:
+ * BSDE_ERR_INVALID_ARG (rank out of range, missing buffer or hook). */
+typedef int (*bsde_exchange_fn)(double* c_dev, int nb, int rank, int nranks, void* stream,
+                                void* user);
+BSDE_API int bsde_set_shard(bsde_ctx* ctx, int rank, int nranks, double* c_dev, size_t c_len,
+                            bsde_exchange_fn exchange, void* user);
+/* The block [*i0, *i1) of rank `rank` (host only, no GPU). */
+BSDE_API int bsde_shard_block(int n, int rank, int nranks, int* i0, int* i1);
 
 /* Basis size p of the current solve parameters, and the multi-indices in
  * the library's order (p x (d+1) ints, graded, lexicographically descending

@@ -29,6 +29,7 @@ ERR_NOMEM = -4
 ERR_NOT_PD = -5
 ERR_TIMEOUT = -6
 ERR_CUDA = -7
+ERR_EXCHANGE = -8
 
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -42,6 +43,8 @@ _dptr = ctypes.POINTER(ctypes.c_double)
 
 alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+exchange_fn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_void_p, ctypes.c_void_p)
 
 
 class bsde_create_opts(ctypes.Structure):
@@ -127,6 +130,10 @@ _SIGNATURES = {
                                     _dptr, _dptr, _dptr, _dptr]),
     "bsde_gram_matrix": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(bsde_solve_params), ctypes.c_int,
                                         _dptr, ctypes.c_int]),
+    "bsde_set_shard": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_size_t, exchange_fn, ctypes.c_void_p]),
+    "bsde_shard_block": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
     "bsde_basis_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_int)]),
     "bsde_basis_indices": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -377,6 +384,31 @@ class Solver:
         self._check(lib().bsde_gram_matrix(self.h, ctypes.byref(p), k, A.ctypes.data_as(_dptr), P * P))
         return A
 
+    def set_shard(self, rank, nranks, xbuf=None, exchange=None):
+        """Run the path kernel on this rank's block of points only
+        (bsde_set_shard).  xbuf: a float64 CUDA tensor of at least
+        nranks * ceil(n / nranks) values (the corrections of every rank);
+        exchange(xbuf, nb, rank, nranks, stream) fills it with every rank's
+        block, ordered on the CUDA stream `stream` (an int handle), e.g.
+        torch_distributed_exchange().  nranks = 1 turns sharding off."""
+        if nranks == 1:
+            self._shard = None
+            return self._check(lib().bsde_set_shard(self.h, 0, 1, None, 0, exchange_fn(), None))
+
+        def _hook(c_dev, nb, rank_, nranks_, stream, user):
+            try:
+                exchange(xbuf, nb, rank_, nranks_, stream or 0)
+                return 0
+            except Exception:  # reported as BSDE_ERR_EXCHANGE
+                import traceback
+                traceback.print_exc()
+                return 1
+
+        cb = exchange_fn(_hook)
+        self._shard = (cb, xbuf, exchange)  # keep alive while the setting holds
+        return self._check(lib().bsde_set_shard(self.h, rank, nranks, xbuf.data_ptr(), xbuf.numel(), cb,
+                                                None))
+
     def basis_size(self, eta=None, q=None):
         eta = self.cfg["eta"] if eta is None else eta
         q = self.cfg.get("q", 1.0) if q is None else q
@@ -417,6 +449,36 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def shard_block(n, rank, nranks):
+    """(i0, i1): the block of points rank `rank` of nranks simulates."""
+    i0, i1 = ctypes.c_int(), ctypes.c_int()
+    rc = lib().bsde_shard_block(n, rank, nranks, ctypes.byref(i0), ctypes.byref(i1))
+    if rc != OK:
+        raise BsdeError(rc, "bsde_shard_block")
+    return i0.value, i1.value
+
+
+def torch_distributed_exchange(group=None):
+    """The exchange of a point-sharded solve over torch.distributed: an
+    all-gather of every rank's block of nb corrections into xbuf (NCCL for
+    CUDA tensors, ordered on the solve's stream; gloo for CPU tensors).
+    Only argument marshalling: the collective is torch.distributed's."""
+    import torch
+    import torch.distributed as dist
+
+    def exchange(xbuf, nb, rank, nranks, stream=0):
+        out = xbuf[:nranks * nb]
+        if out.is_cuda:
+            with torch.cuda.stream(torch.cuda.ExternalStream(int(stream), device=out.device)):
+                mine = out[rank * nb:(rank + 1) * nb].clone()
+                dist.all_gather_into_tensor(out, mine, group=group)
+        else:
+            mine = out[rank * nb:(rank + 1) * nb].clone()
+            dist.all_gather(list(out.split(nb)), mine, group=group)
+
+    return exchange
 
 
 def basis_indices(d, eta, q=1.0):

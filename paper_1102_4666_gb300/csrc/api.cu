@@ -225,6 +225,30 @@ int bsde_gram_matrix(bsde_ctx* c, const bsde_solve_params* prm, int k, double* A
   })
 }
 
+int bsde_set_shard(bsde_ctx* c, int rank, int nranks, double* c_dev, size_t c_len,
+                   bsde_exchange_fn exchange, void* user) {
+  if (!c) return BSDE_ERR_INVALID_ARG;
+  if (nranks < 1 || rank < 0 || rank >= nranks)
+    return fail(c, BSDE_ERR_INVALID_ARG, "set_shard: rank out of range");
+  if (nranks > 1 && (!c_dev || !exchange))
+    return fail(c, BSDE_ERR_INVALID_ARG, "set_shard: nranks > 1 needs a buffer and an exchange hook");
+  Problem& P = c->prob;
+  P.destroy_graph();
+  P.sh_rank = nranks > 1 ? rank : 0;
+  P.sh_n = nranks;
+  P.sh_buf = nranks > 1 ? c_dev : nullptr;
+  P.sh_len = nranks > 1 ? c_len : 0;
+  P.sh_fn = nranks > 1 ? exchange : nullptr;
+  P.sh_user = user;
+  return BSDE_OK;
+}
+
+int bsde_shard_block(int n, int rank, int nranks, int* i0, int* i1) {
+  if (n < 0 || nranks < 1 || rank < 0 || rank >= nranks || !i0 || !i1) return BSDE_ERR_INVALID_ARG;
+  shard_block(n, rank, nranks, *i0, *i1);
+  return BSDE_OK;
+}
+
 int bsde_basis_size(int d, int eta, double q, int* p_out) {
   if (d < 1 || d > BSDE_MAX_D || eta < 0 || eta > 15 || !(q > 0.0) || q > 1.0 || !p_out)
     return BSDE_ERR_INVALID_ARG;

@@ -144,6 +144,9 @@ struct GridHost {
 struct ProblemDev {
   int n = 0, n_pad = 0, p = 0, p_pad = 0, eta = 0, chunks = 0;
   int gram_splits = 0;        // K splits of the tensor-core Gram (mixed)
+  // point sharding: the path kernel and the per-point reduction cover the
+  // points [shard_i0, shard_i0 + shard_n) only (shard_n = 0: all n points)
+  int shard_i0 = 0, shard_n = 0;
   double* t = nullptr;        // [n]
   double* x = nullptr;        // [d][n]
   double* B = nullptr;        // [p][n_pad] FP64 basis matrix, point index fastest

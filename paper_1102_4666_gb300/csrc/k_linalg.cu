@@ -12,10 +12,10 @@
 namespace {
 
 // eq. chat: c_i = (1/M) sum of the per-chunk sums, in chunk order
-__global__ void k_reduce_c(int n, int chunks, int M, const double* __restrict__ partial,
+__global__ void k_reduce_c(int i0, int count, int chunks, int M, const double* __restrict__ partial,
                            double* __restrict__ c) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= i0 + count) return;
   double s = 0.0;
   for (int q = 0; q < chunks; ++q) s += partial[(size_t)i * chunks + q];
   c[i] = s / (double)M;
@@ -468,7 +468,9 @@ void launch_cheb2mono(const ProblemDev& P, cudaStream_t st) {
 }
 
 void launch_reduce_c(const ProblemDev& P, int M, cudaStream_t st) {
-  k_reduce_c<<<(P.n + 255) / 256, 256, 0, st>>>(P.n, P.chunks, M, P.partial, P.c);
+  const int count = P.shard_n > 0 ? P.shard_n : P.n;
+  if (count <= 0) return;
+  k_reduce_c<<<(count + 255) / 256, 256, 0, st>>>(P.shard_i0, count, P.chunks, M, P.partial, P.c);
 }
 
 void launch_gram_f64(const ProblemDev& P, cudaStream_t st) {

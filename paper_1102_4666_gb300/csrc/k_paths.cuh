@@ -57,6 +57,7 @@ struct Args {
   R Cp[D + 1][D + 1];  // correlation padded with a zero time row/column
   R ctr[D + 1], sc[D + 1];  // xi_v = (y_v - ctr_v) sc_v
   int N, M, n, p, eta, chunks, tpb, ppt, tab_stride;
+  int i0;           // first point of the launch (a block of the points when sharded)
   int payoff, obstacle, vol_sin;
   R vb;
   R rho;  // constant correlation (dense evaluation)
@@ -552,8 +553,9 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
   const int tid = threadIdx.x;
   const int tpb = a.tpb;
   const int item = blockIdx.x;
-  const int i = item / a.chunks;
-  const int chunk = item - i * a.chunks;
+  const int il = item / a.chunks;
+  const int chunk = item - il * a.chunks;
+  const int i = a.i0 + il;
 
   // shared memory carve-up (dense evaluation: no multi-index or Chebyshev
   // tables; alpha holds the monomial coefficients, p of them)
@@ -920,6 +922,7 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
   a.tpb = tpb;
   a.ppt = ppt;
   a.chunks = P.chunks;
+  a.i0 = P.shard_i0;
   // tanh families: (A_j, B_j) pairs, rows padded to 4 values (16 bytes in
   // FP32) so that one 128-bit load fetches two assets' pairs
   a.tab_stride = (m.vol_kind == 1 || m.vol_kind == 2) ? ((2 * D + 3) & ~3) : (D < 3 ? 3 : D);
@@ -955,7 +958,10 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
                  : (m.vol_kind == 1) ? VK_TANH_ABS
                  : (m.vol_kind == 3) ? VK_DUPIRE
                                      : VK_TANH;
-  const unsigned grid = (unsigned)P.n * (unsigned)P.chunks;
+  // the points of this launch: all n, or the block [shard_i0, shard_i0 + shard_n)
+  const int npts = P.shard_n > 0 ? P.shard_n : P.n;
+  if (npts <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)npts * (unsigned)P.chunks;
   if (dense) {  // implies a constant correlation
     // the host selects: degree <= 3 loops (any d), degree-4 loops (d <= 5),
     // the tree recursion of degree 4 (d >= 6) or 5 and 6 (d <= 5)

@@ -87,6 +87,13 @@ int device_sm_count() {
   return cache[dev];
 }
 
+void shard_block(int n, int rank, int nranks, int& i0, int& i1) {
+  const int nb = (n + nranks - 1) / nranks;
+  const long long a = (long long)rank * nb, b = a + nb;
+  i0 = (int)(a < n ? a : n);
+  i1 = (int)(b < n ? b : n);
+}
+
 static bool is_fin(double v) { return std::isfinite(v); }
 
 // Cholesky-Banachiewicz of the d x d correlation (C = L L^*, Section 6.2)
@@ -452,6 +459,7 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
     }
     P.partial = (double*)take((size_t)n * s.chunks * 8);
     P.c = (double*)take((size_t)n * 8);
+    c_own = P.c;
     P.rhs = (double*)take((size_t)p * 8 * 4);
     P.delta = P.rhs + p;
     P.res = P.rhs + 2 * p;
@@ -511,6 +519,23 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   }
   shape = s;
   dev.chunks = s.chunks;
+  // point sharding: this rank's block, and the corrections in the caller's
+  // exchange buffer
+  dev.c = c_own;
+  dev.shard_i0 = 0;
+  dev.shard_n = 0;
+  if (sh_n > 1) {
+    const int nb = (n + sh_n - 1) / sh_n;
+    if (!sh_buf || sh_len < (size_t)nb * sh_n) {
+      err = "solve: the shard exchange buffer holds fewer than nranks * ceil(n / nranks) values";
+      return BSDE_ERR_INVALID_ARG;
+    }
+    int i0, i1;
+    shard_block(n, sh_rank, sh_n, i0, i1);
+    dev.c = sh_buf;
+    dev.shard_i0 = i0;
+    dev.shard_n = i1 - i0;
+  }
   // tables, read-out point, key
   cudaError_t e = cudaMemcpyAsync(dev.pairs, pairs.data(), (size_t)p * 8, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dev.nnz, nnz.data(), (size_t)p, cudaMemcpyHostToDevice, st);
@@ -617,6 +642,20 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
   }
   if (rec) record(ev[1], st);
   launch_reduce_c(dev, shape.M, st);
+  if (sh_n > 1) {
+    // every rank's block of corrections into the exchange buffer
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      err = std::string("kernel launch failed: ") + cudaGetErrorString(e);
+      return BSDE_ERR_CUDA;
+    }
+    const int nb = (shape.n + sh_n - 1) / sh_n;
+    const int rc = sh_fn(sh_buf, nb, sh_rank, sh_n, (void*)st, sh_user);
+    if (rc != 0) {
+      err = "solve: the exchange hook failed (status " + std::to_string(rc) + ")";
+      return BSDE_ERR_EXCHANGE;
+    }
+  }
   if (rec) record(ev[2], st);
   if (shape.qr) {
     // refit by pivoted QR on the design matrix (FP64)
@@ -703,7 +742,7 @@ int Problem::start(const bsde_solve_params& prm, Allocator& al, size_t budget, c
     return BSDE_ERR_STATE;
   }
   cudaMemsetAsync(dev.out + OUT_PRICE_IT, 0, 3 * 64 * 8, st);
-  if (prm.use_graph) {
+  if (prm.use_graph && sh_n == 1) {
     std::ostringstream os;
     os << shape.d << ' ' << shape.n << ' ' << shape.p << ' ' << shape.M << ' ' << shape.N << ' '
        << prm.K_it << ' ' << prm.k_start << ' ' << prm.refine_steps << ' ' << prm.timing << ' '
@@ -860,6 +899,7 @@ void Problem::release(Allocator& al, cudaStream_t st) {
   destroy_graph();
   if (block) al.put(block, st);
   block = nullptr;
+  c_own = nullptr;
   block_bytes = 0;
   if (fact) al.put(fact, st);
   fact = nullptr;

@@ -48,6 +48,13 @@ class Problem {
   std::vector<int> conv_row, conv_l;
   std::vector<double> conv_c;
   std::string err;
+  // point sharding (bsde_set_shard): rank sh_rank of sh_n, the caller's
+  // correction buffer and exchange hook
+  int sh_rank = 0, sh_n = 1;
+  double* sh_buf = nullptr;
+  size_t sh_len = 0;
+  bsde_exchange_fn sh_fn = nullptr;
+  void* sh_user = nullptr;
 
   ~Problem();
   // validate params, build the basis, (re)allocate device memory; BSDE_OK or an error
@@ -87,6 +94,7 @@ class Problem {
  private:
   void* block = nullptr;
   size_t block_bytes = 0;
+  double* c_own = nullptr;  // the corrections in the context's own arena
   Shape alloc_shape;
   // Gram matrices, Cholesky factors and inverses of up to nfact iterations
   void* fact = nullptr;
@@ -111,3 +119,5 @@ int bsde_set_model_impl(ModelHost& m, const bsde_sigma* sigma, double r, const b
                         const bsde_penalty* penalty, std::string& err);
 int bsde_set_grid_impl(GridHost& g, int d, int n, const double* lo, const double* hi,
                        int resample, std::string& err);
+// block [i0, i1) of the points of rank `rank` of nranks: nb = ceil(n / nranks)
+void shard_block(int n, int rank, int nranks, int& i0, int& i1);

@@ -90,7 +90,7 @@ CASES = [
     ("c4", {}, 125),                        # one K-block of 32 points per slice
     ("c3", {}, 63),                         # the same for d = 5 (n_pad = 2016)
     ("c3", {}, 0),                          # d = 5, p = 210, n = 2000
-    ("c4", dict(n=1001, eta=4), 0),         # p = 1365 (11 x 11 tiles), ragged n
+    ("c4", dict(n=2801, eta=4), 0),         # p = 1365 (11 x 11 tiles), ragged n
     ("c2", dict(n=77), 0),                  # p = 28 < one tile, n not a multiple of 32
     ("c4", dict(n=700, eta=5, q=0.6), 3),   # hyperbolic set (eq. hyper_set), p = 221
 ]
