@@ -97,19 +97,19 @@ def test_shard_blocks_tile_the_points(G):
 
 def test_failed_exchange_is_reported_and_the_context_stays_usable(G):
     import torch
-    cfg = workloads.config("c4", n=120, M=64, N=4, eta=2, K_it=2, **{"lambda": 1.0})
+    cfg = workloads.config("c4", n=200, M=64, N=4, eta=2, K_it=2, **{"lambda": 1.0})
     s = G.Solver(cfg, precision="mixed")
     ref = s.solve()
 
     def broken(xbuf, nb, rank, nranks, stream):
         raise RuntimeError("peer lost")
 
-    xbuf = torch.zeros(2 * 60, dtype=torch.float64, device="cuda")
+    xbuf = torch.zeros(2 * 100, dtype=torch.float64, device="cuda")
     s.set_shard(0, 2, xbuf, broken)
     rep = s.solve(check=False)
     assert rep.status == G.ERR_EXCHANGE
     # too small an exchange buffer is refused before any device work
-    s.set_shard(1, 2, xbuf[:100], broken)
+    s.set_shard(1, 2, xbuf[:150], broken)
     assert s.solve(check=False).status == G.ERR_INVALID_ARG
     s.set_shard(0, 1)
     again = s.solve()
