@@ -374,7 +374,8 @@ def run_ours(args):
     from paper_1102_4666_gb300 import autotune
     shape = autotune.lookup(cfg, "mixed") or autotune.tune(cfg, "mixed", repeats=3)
     stream = torch.cuda.Stream(device=dev)
-    s = G.Solver(cfg, precision="mixed", device=local, stream=stream.cuda_stream, launch_shape=shape)
+    s = G.Solver(cfg, precision="mixed", device=local, stream=stream.cuda_stream, launch_shape=shape,
+                 gram_splits=autotune.lookup_gram_splits(cfg, "mixed"))
     if shard:
         # one problem, its points in blocks over the ranks, one all-gather of
         # the corrections per iteration (strong scaling)
@@ -519,7 +520,8 @@ def run_ours(args):
                    "parallelism": ("points sharded over %d ranks, one all-gather of the corrections "
                                    "per iteration" % world) if shard else
                                   ("one independent problem per rank" if world > 1 else "one GPU"),
-                   "paths_launch_shape": list(shape) if shape else None},
+                   "paths_launch_shape": list(shape) if shape else None,
+                   "gram_splits": autotune.lookup_gram_splits(cfg, "mixed") or "default (one wave)"},
         "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,EV_DENSE3,CC,float,10>",
                      "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,

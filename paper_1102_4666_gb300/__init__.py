@@ -261,8 +261,10 @@ def solve_params(cfg, seed=None, K_it=None, k_start=0, refine_steps=-1, use_grap
     return p
 
 
-def request(cfg, seed=None, use_graph=1):
-    """A bsde_request (and its keep-alive list) from a workload dictionary."""
+def request(cfg, seed=None, use_graph=1, precision=None):
+    """A bsde_request (and its keep-alive list) from a workload dictionary.
+    With a precision, the launch shape and Gram split count tuned for the
+    request's problem class (autotune cache) go into its parameters."""
     sg, r, pf, pen, keep = model_structs(cfg)
     rq = bsde_request()
     rq.sigma, rq.r, rq.payoff, rq.penalty = sg, r, pf, pen
@@ -270,7 +272,14 @@ def request(cfg, seed=None, use_graph=1):
     for v in range(cfg["d"] + 1):
         rq.lo[v] = cfg["lo"][v]
         rq.hi[v] = cfg["hi"][v]
-    rq.params = solve_params(cfg, seed=seed, use_graph=use_graph)
+    kw = {}
+    if precision is not None:
+        from . import autotune
+        shape = autotune.lookup(cfg, precision)
+        if shape:
+            kw["paths_tpb"], kw["paths_ppt"] = shape
+        kw["gram_splits"] = autotune.lookup_gram_splits(cfg, precision)
+    rq.params = solve_params(cfg, seed=seed, use_graph=use_graph, **kw)
     return rq, keep
 
 
@@ -304,11 +313,13 @@ class Solver:
     """One context of the C ABI set up from a workload dictionary."""
 
     def __init__(self, cfg, precision="mixed", device=0, stream=None, torch_memory=True, mem_budget=0,
-                 launch_shape=None, allocator=None):
+                 launch_shape=None, allocator=None, gram_splits=0):
         self.cfg = cfg
         # (threads per CTA, paths per thread) of the path kernel, e.g. from
         # autotune.lookup()/tune(); None leaves the library's choice
         self.launch_shape = launch_shape
+        # split count of the tensor-core Gram (autotune.lookup_gram_splits; 0: default)
+        self.gram_splits = gram_splits
         o = bsde_create_opts()
         o.device = device
         o.stream = stream
@@ -347,6 +358,8 @@ class Solver:
     def _shape(self, kw):
         if self.launch_shape and "paths_tpb" not in kw and "paths_ppt" not in kw:
             kw = dict(kw, paths_tpb=self.launch_shape[0], paths_ppt=self.launch_shape[1])
+        if self.gram_splits and "gram_splits" not in kw:
+            kw = dict(kw, gram_splits=self.gram_splits)
         return kw
 
     def solve(self, check=True, **kw):
@@ -509,6 +522,7 @@ class Server:
         o.policy = {"fifo": POLICY_FIFO, "shortest": POLICY_SHORTEST,
                     "response_ratio": POLICY_RESPONSE_RATIO}[policy]
         o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+        self.precision = precision
         h = ctypes.c_void_p()
         rc = lib().bsde_server_create(ctypes.byref(h), ctypes.byref(o))
         if rc != OK:
@@ -516,7 +530,9 @@ class Server:
         self.h = h
 
     def submit(self, cfg, seed=None):
-        rq, keep = request(cfg, seed=seed)
+        # the request's class is looked up in the autotune cache: its tuned
+        # path-kernel launch shape and Gram split count, when tuned
+        rq, keep = request(cfg, seed=seed, precision=self.precision)
         rid = ctypes.c_uint64()
         rc = lib().bsde_server_submit(self.h, ctypes.byref(rq), ctypes.byref(rid))
         if rc != OK:

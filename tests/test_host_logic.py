@@ -31,6 +31,34 @@ def test_autotune_cache_round_trip(tmp_path, monkeypatch):
     assert autotune.lookup(workloads.config("c4"), "mixed") is None
 
 
+def test_server_requests_take_the_tuned_shapes(tmp_path, monkeypatch):
+    """The serving binding builds each request's parameters with the launch
+    shape and Gram split count tuned for its problem class, and the library
+    defaults (0) for a class that was not tuned."""
+    import paper_1102_4666_gb300 as G
+    from paper_1102_4666_gb300 import autotune
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("BSDE_TUNE_CACHE", str(path))
+    c4 = workloads.config("c4")
+    path.write_text(json.dumps({autotune.key(c4, "mixed"): {"shape": [64, 8], "ms_paths": 1.0,
+                                                             "gram_splits": 50}}))
+    rq, _ = G.request(c4, precision="mixed")
+    assert (rq.params.paths_tpb, rq.params.paths_ppt, rq.params.gram_splits) == (64, 8, 50)
+    assert autotune.lookup_gram_splits(c4, "mixed") == 50
+    rq, _ = G.request(workloads.config("c3"), precision="mixed")
+    assert (rq.params.paths_tpb, rq.params.paths_ppt, rq.params.gram_splits) == (0, 0, 0)
+    rq, _ = G.request(c4, precision="fp64")
+    assert (rq.params.paths_tpb, rq.params.paths_ppt) == (0, 0)
+
+
+def test_gram_split_candidates():
+    from paper_1102_4666_gb300 import autotune
+    c4 = workloads.config("c4")  # p = 364: 6 upper tiles; n = 4000: 125 K-blocks
+    assert autotune.gram_split_candidates(c4, 152) == [0, 12, 50, 100]
+    small = workloads.config("c4", n=200, eta=2)  # p = 78: 1 tile; 7 K-blocks
+    assert autotune.gram_split_candidates(small, 152) == [0, 7]
+
+
 def test_serving_mix_is_seeded_and_respects_its_ranges():
     a = workloads.serving_mix(300, seed=7)
     b = workloads.serving_mix(300, seed=7)
@@ -95,17 +123,21 @@ def test_autotune_keeps_the_fastest_shape_and_skips_failing_ones(tmp_path, monke
     path = tmp_path / "tune.json"
     monkeypatch.setenv("BSDE_TUNE_CACHE", str(path))
     times = {(128, 4): 5.0, (256, 2): 3.0, (64, 8): 4.0}
+    gram_ms = {0: 0.5, 7: 0.3}
     probes = []
 
     class Report:
-        def __init__(self, ms):
+        def __init__(self, ms, ms_gram=1.0):
             self.ms_paths = ms
+            self.ms_gram = ms_gram
 
     class StandIn:
         def __init__(self, cfg, precision="mixed"):
             probes.append((cfg["K_it"], cfg["n"], precision))
 
-        def solve(self, use_graph=1, timing=0, paths_tpb=0, paths_ppt=0):
+        def solve(self, use_graph=1, timing=0, paths_tpb=0, paths_ppt=0, gram_splits=None):
+            if gram_splits is not None:
+                return Report(1.0, gram_ms[gram_splits])
             if (paths_tpb, paths_ppt) not in times:
                 raise RuntimeError("launch failed")
             return Report(times[(paths_tpb, paths_ppt)])
@@ -114,13 +146,18 @@ def test_autotune_keeps_the_fastest_shape_and_skips_failing_ones(tmp_path, monke
             pass
 
     monkeypatch.setattr(G, "Solver", StandIn)
+    monkeypatch.setattr(autotune, "_sm_count", lambda: 152)
     cfg = workloads.config("c3")
+    # p = 210 (3 upper tiles: one wave is 50 slices) and 300 points (10 K-blocks):
+    # candidates 0 and 10 slices ... capped by the K-blocks
+    gram_ms[10] = 0.3
     best = autotune.tune(cfg, "mixed", candidates=[(128, 4), (256, 2), (32, 32), (64, 8)], n_points=300)
     assert best == (256, 2)
-    assert probes == [(1, 300, "mixed")]
+    assert probes == [(1, 300, "mixed"), (1, 300, "mixed")]
     assert autotune.lookup(cfg, "mixed") == (256, 2)
     entry = json.loads(path.read_text())[autotune.key(cfg, "mixed")]
     assert entry["ms_paths"] == 3.0 and set(entry["candidates"]) == {"128x4", "256x2", "64x8"}
+    assert entry["gram_splits"] == 10 and autotune.lookup_gram_splits(cfg, "mixed") == 10
 
     path.unlink()
     assert autotune.tune(cfg, "mixed", candidates=[(32, 32)]) is None
