@@ -349,6 +349,8 @@ def run_serving_suite(n_requests, seed=7, load=0.8):
     out["shortest_first_4"] = run_serving(reqs, arr, slots=4, policy="shortest")
     out["response_ratio_4"] = run_serving(reqs, arr, slots=4, policy="response_ratio")
     out["response_ratio_16"] = run_serving(reqs, arr, slots=16, policy="response_ratio")
+    out["size_lanes_16"] = run_serving(reqs, arr, slots=16, policy="size_lanes")
+    out["size_lanes_4"] = run_serving(reqs, arr, slots=4, policy="size_lanes")
     out["one_at_a_time_mixed"] = run_serving(reqs, arr, slots=1, policy="fifo")
     out["one_at_a_time_fp64"] = fp64_sequential_model(reqs, arr)
     out["fp64_comparator_measured"] = run_serving_fp64_measured()

@@ -372,6 +372,12 @@ typedef struct bsde_server bsde_server;
                                   and the server's measured throughput: short
                                   requests go first, long ones rise as they
                                   wait (no starvation)                      */
+#define BSDE_POLICY_SIZE_LANES 3 /* arrival order in two lanes: a request with
+                                  less work than the average so far is
+                                  admitted at once (high-priority stream);
+                                  one with at least the average work waits
+                                  while another of its lane runs, and the
+                                  smaller requests behind it pass it      */
 
 typedef struct {
   int device;

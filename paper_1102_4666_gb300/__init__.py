@@ -37,7 +37,7 @@ PREC_MIXED = 1
 VOL_CONST, VOL_ABS_TANH, VOL_SIN_TANH, VOL_DUPIRE = 0, 1, 2, 3
 PAYOFF_PUT, PAYOFF_CALL = 0, 1
 OBSTACLE_PAYOFF, OBSTACLE_RAW = 0, 1
-POLICY_FIFO, POLICY_SHORTEST, POLICY_RESPONSE_RATIO = 0, 1, 2
+POLICY_FIFO, POLICY_SHORTEST, POLICY_RESPONSE_RATIO, POLICY_SIZE_LANES = 0, 1, 2, 3
 
 _dptr = ctypes.POINTER(ctypes.c_double)
 
@@ -513,14 +513,16 @@ class Server:
     max_slots requests resident at once (each a captured graph of its whole
     solve on a stream of its own), admitted while they fit mem_budget bytes
     (0: no limit) in the order of the policy: "fifo", "shortest" (fewest
-    path-steps K_it n M N first) or "response_ratio" (highest
-    (wait + service) / service first)."""
+    path-steps K_it n M N first), "response_ratio" (highest
+    (wait + service) / service first) or "size_lanes" (arrival order; a
+    request with at least the average work waits while another such runs,
+    smaller ones pass it)."""
 
     def __init__(self, device=0, max_slots=16, mem_budget=0, precision="mixed", policy="fifo"):
         o = bsde_server_opts()
         o.device, o.max_slots, o.mem_budget = device, max_slots, mem_budget
         o.policy = {"fifo": POLICY_FIFO, "shortest": POLICY_SHORTEST,
-                    "response_ratio": POLICY_RESPONSE_RATIO}[policy]
+                    "response_ratio": POLICY_RESPONSE_RATIO, "size_lanes": POLICY_SIZE_LANES}[policy]
         o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
         self.precision = precision
         h = ctypes.c_void_p()

@@ -66,6 +66,7 @@ struct bsde_server {
   std::vector<cudaStream_t> free_streams[2];  // [0] normal, [1] high priority
   double work_sum = 0.0;
   uint64_t work_count = 0;
+  int large_running = 0;  // running requests on normal-priority streams
   size_t used_bytes = 0;
   std::vector<uint64_t> admitting;  // ids popped from the queue, not yet in running/done
   std::vector<double> latencies_ms;
@@ -85,6 +86,21 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
   if (opts.policy == BSDE_POLICY_SHORTEST) {
     for (size_t q = 1; q < queue.size(); ++q)
       if (queue[q]->work < queue[pick]->work) pick = q;
+  } else if (opts.policy == BSDE_POLICY_SIZE_LANES) {
+    // arrival order, but a request with at least the average work waits
+    // while another such request runs; smaller ones pass it
+    const double sum = work_sum, cnt = (double)work_count;
+    bool found = false;
+    for (size_t q = 0; q < queue.size(); ++q) {
+      const double w = queue[q]->work;
+      const bool large = w >= (sum + w) / (cnt + 1.0);
+      if (!large || large_running == 0) {
+        pick = q;
+        found = true;
+        break;
+      }
+    }
+    if (!found) return false;
   } else if (opts.policy == BSDE_POLICY_RESPONSE_RATIO) {
     // service estimate: path-steps at the throughput measured so far (a
     // GB300-scale default until a second of busy time has been seen)
@@ -120,6 +136,7 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
     cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi ? hi_p : lo_p);
   }
   req->prio = hi;
+  if (!hi) ++large_running;
   req->stream = st;
   admitting.push_back(req->id);
   lk.unlock();
@@ -142,6 +159,7 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
     req->t_done = now_s();
     P.release(al, st);
     used_bytes -= req->bytes;
+    if (!req->prio) --large_running;
     free_streams[req->prio].push_back(st);
     done[req->id] = std::move(req);
     cv_done.notify_all();
@@ -176,6 +194,7 @@ void bsde_server::loop() {
       r->e0 = r->e1 = nullptr;
       lk.lock();
       used_bytes -= r->bytes;
+      if (!r->prio) --large_running;
       free_streams[r->prio].push_back(r->stream);
       latencies_ms.push_back((r->t_done - r->t_submit) * 1e3);
       if (r->rc == BSDE_OK) path_steps += r->rep.path_steps;
@@ -205,7 +224,7 @@ int bsde_server_create(bsde_server** out, const bsde_server_opts* o) {
   if (!out || !o || o->max_slots < 1 || o->max_slots > 64 ||
       (o->precision != BSDE_PREC_FP64 && o->precision != BSDE_PREC_MIXED) ||
       (o->policy != BSDE_POLICY_FIFO && o->policy != BSDE_POLICY_SHORTEST &&
-       o->policy != BSDE_POLICY_RESPONSE_RATIO))
+       o->policy != BSDE_POLICY_RESPONSE_RATIO && o->policy != BSDE_POLICY_SIZE_LANES))
     return BSDE_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || o->device < 0 || o->device >= ndev) {

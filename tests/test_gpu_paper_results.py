@@ -1,12 +1,29 @@
 """End-to-end accuracy of the solver on the paper's own experiments
 (Section 6): the prices and deltas it prints (tests/golden/paper_results.txt).
 
-The paper does not state its domain D; a box log S0 +- w with w of a few
-tenths (given per case) reproduces its numbers, whereas the wide box of the
-throughput workloads (w = 1.5) does not (the degree-3 fit over a wide box has
-a large projection error at (0, x0)).  The tolerances allow for Monte Carlo
-noise (different random numbers from the paper's) and for the iterates'
-fluctuation: the mean of the last iterates is compared."""
+One stated rule fixes the domain D of every case (the paper does not give
+it): D_j = [log S0_j - s_j, log S0_j + s_j] with s_j = sigma_j sqrt(T), one
+standard deviation of the terminal log-price (sigma_j the volatility at the
+money: the constant sigma, or sigma(0, S0) = 0.6 (1.2 - 1) = 0.12 for the
+local volatility of eq. vol_locale), and t in [0, T].
+
+Each case is solved with SEEDS independent seeds; the result of one solve is
+the mean of the price over the second half of the Picard iterates (the
+iterates fluctuate around the fixed point by the Monte Carlo error), and the
+test compares the mean over the seeds with the paper's number:
+
+    |mean - benchmark| <= CI half-width + 3 SE,
+
+SE the standard error of the mean over the seeds.  Nothing else is allowed
+for: the time discretisation is exact for the Black-Scholes cases (constant
+sigma: the log-Euler step is the exact law, N = 2 as in Section 6.2) and the
+Picard truncation after 10 iterations is below 1e-6 for these drivers.  The
+remaining bias is the projection error of the degree-3 (or hyperbolic) fit
+on D, which depends on D; on the rule's box it exceeds the paper's interval
+for the cases marked xfail below (their measured offsets and the results as
+functions of the box width are tabulated in the design notes).
+"""
+import math
 import os
 
 import numpy as np
@@ -16,6 +33,7 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_results.txt")
+SEEDS = 8
 
 
 def golden():
@@ -28,50 +46,91 @@ def golden():
     return out
 
 
-def solve(cfg):
+def half_width(sigma_atm, T):
+    """The domain rule: one standard deviation of the terminal log-price."""
+    return sigma_atm * math.sqrt(T)
+
+
+def runs(cfg, field="price"):
+    """Per-seed results: the mean price over the second half of the
+    iterates, or the mean delta over the assets after the last iterate."""
     import paper_1102_4666_gb300 as G
-    s = G.Solver(cfg, precision="mixed")
-    rep = s.solve(use_graph=0)
-    s.close()
-    assert rep.status == G.OK
-    return rep
+    vals = []
+    for j in range(SEEDS):
+        c = dict(cfg)
+        c["seed"] = 100 + j
+        s = G.Solver(c, precision="mixed")
+        rep = s.solve(use_graph=0)
+        s.close()
+        assert rep.status == G.OK
+        K = cfg["K_it"]
+        if field == "price":
+            vals.append(float(np.mean(rep.price_iter[K // 2:K])))
+        else:
+            vals.append(float(np.mean(rep.delta[:cfg["d"]])))
+    v = np.array(vals)
+    return v.mean(), v.std(ddof=1) / math.sqrt(len(v))
 
 
+def check(mean, se, bench, lo, hi):
+    ci = 0.5 * (hi - lo)
+    err = abs(mean - bench)
+    assert err <= ci + 3.0 * se, "mean %.5f +- %.5f (SE) vs %.5f (CI +- %.5f)" % (mean, se, bench, ci)
+
+
+@pytest.mark.xfail(reason="projection bias of the degree-3 fit on the rule's box: +0.08 (4 %) above the "
+                          "paper's interval", strict=False)
 def test_european_put_d5():
-    ref = golden()[("euro_put_d5", "price")][0]
+    bench, lo, hi = golden()[("euro_put_d5", "price")]
     cfg = workloads.make(d=5, T=3.0, r=0.05, K=100, S0=100, vol={"kind": "const", "a": 0.2}, rho=0.1,
-                         lam=0.0, n=1000, M=50000, N=2, eta=3, K_it=10, seed=11, half_width=0.25)
-    rep = solve(cfg)
-    tail = np.mean(rep.price_iter[5:10])
-    assert abs(tail - ref) < 0.015 * ref, tail
+                         lam=0.0, n=1000, M=50000, N=2, eta=3, K_it=10, seed=11,
+                         half_width=half_width(0.2, 3.0))
+    check(*runs(cfg), bench, lo, hi)
 
 
+@pytest.mark.xfail(reason="projection bias of the hyperbolic fit on the rule's box: +0.035 (0.5 %) above "
+                          "the paper's interval", strict=False)
 def test_european_call_d10_hyperbolic():
-    ref = golden()[("euro_call_d10", "price")][0]
+    bench, lo, hi = golden()[("euro_call_d10", "price")]
     cfg = workloads.make(d=10, T=1.0, r=0.05, K=100, S0=100, vol={"kind": "const", "a": 0.2}, rho=0.2,
                          lam=0.0, n=1000, M=30000, N=2, eta=5, q=0.6, K_it=10, seed=12,
-                         half_width=0.2, payoff="call")
-    rep = solve(cfg)
-    assert rep.p == 221
-    tail = np.mean(rep.price_iter[5:10])
-    assert abs(tail - ref) < 0.02 * ref, tail
+                         half_width=half_width(0.2, 1.0), payoff="call")
+    check(*runs(cfg), bench, lo, hi)
 
 
-def test_dupire_put_d5():
-    g = golden()
-    ref, dref = g[("dupire_put_d5", "price")][0], g[("dupire_put_d5", "delta")][0]
+def test_dupire_put_d5_price():
+    bench, lo, hi = golden()[("dupire_put_d5", "price")]
     cfg = workloads.make(d=5, T=1.0, r=0.05, K=100, S0=100, vol={"kind": "dupire", "s": 100.0}, rho=0.0,
-                         lam=0.0, n=1000, M=30000, N=10, eta=3, K_it=10, seed=13, half_width=0.15)
-    rep = solve(cfg)
-    tail = np.mean(rep.price_iter[5:10])
-    assert abs(tail - ref) < 0.04 * ref, tail
-    assert abs(np.mean(rep.delta[:5]) - dref) < 0.25 * abs(dref)
+                         lam=0.0, n=1000, M=30000, N=10, eta=3, K_it=10, seed=13,
+                         half_width=half_width(0.12, 1.0))
+    check(*runs(cfg), bench, lo, hi)
+
+
+@pytest.mark.xfail(reason="the per-asset delta on the rule's box is -0.051, 18 % below the paper's -0.0625 "
+                          "(the paper does not say which derivative it prints)", strict=False)
+def test_dupire_put_d5_delta():
+    """The paper prints the benchmark delta -0.0625 without an interval; its
+    price interval is 0.92 % wide (+-0.46 %), and a delta interval of the
+    same relative width is used.  The delta is read as dV/dS_j of one asset
+    (by symmetry they are equal; their mean is compared)."""
+    g = golden()
+    dref = g[("dupire_put_d5", "delta")][0]
+    cfg = workloads.make(d=5, T=1.0, r=0.05, K=100, S0=100, vol={"kind": "dupire", "s": 100.0}, rho=0.0,
+                         lam=0.0, n=1000, M=30000, N=10, eta=3, K_it=10, seed=13,
+                         half_width=half_width(0.12, 1.0))
+    mean, se = runs(cfg, "delta")
+    check(mean, se, dref, dref - 0.0046 * abs(dref), dref + 0.0046 * abs(dref))
 
 
 def test_american_put_d5_deltas():
-    ref = np.mean(golden()[("amer_put_d5", "delta5")])
+    """The delta table of Section 6.2.2 gives the five assets' deltas at
+    iteration 5 of one run; their mean is compared, with the standard error
+    of that mean (their spread) as the paper's interval."""
+    d5 = np.array(golden()[("amer_put_d5", "delta5")])
+    bench = d5.mean()
+    ci = 3.0 * d5.std(ddof=1) / math.sqrt(len(d5))
     cfg = workloads.make(d=5, T=1.0, r=0.05, K=100, S0=100, vol={"kind": "const", "a": 0.25}, rho=0.2,
-                         lam=1.0, n=1000, M=5000, N=2, eta=3, K_it=5, seed=14, half_width=0.25, div=0.1)
-    rep = solve(cfg)
-    d = np.mean(rep.delta[:5])
-    assert abs(d - ref) < 0.03 * abs(ref), d
+                         lam=1.0, n=1000, M=5000, N=2, eta=3, K_it=5, seed=14,
+                         half_width=half_width(0.25, 1.0), div=0.1)
+    mean, se = runs(cfg, "delta")
+    check(mean, se, bench, bench - ci, bench + ci)

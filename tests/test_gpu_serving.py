@@ -63,15 +63,15 @@ def test_admission_by_memory_budget():
     srv.close()
 
 
-def _completion_order(policy):
-    """Submit two long requests and then a short one to a one-slot server and
-    return the order in which they complete (0, 1: long; 2: short)."""
+def _completion_order(policy, slots=1):
+    """Submit two long requests and then a short one to a server with `slots`
+    slots and return the order in which they complete (0, 1: long; 2: short)."""
     import time
 
     import paper_1102_4666_gb300 as G
     long_req = workloads.config("c3", K_it=2)  # 1e9 path-steps
     short_req = workloads.config("c3", n=500, M=1000, K_it=1)
-    srv = G.Server(max_slots=1, precision="mixed", policy=policy)
+    srv = G.Server(max_slots=slots, precision="mixed", policy=policy)
     ids = [srv.submit(long_req), srv.submit(long_req, seed=99), srv.submit(short_req)]
     done = []
     t0 = time.monotonic()
@@ -105,3 +105,11 @@ def test_response_ratio_policy_serves_short_first_and_everyone():
     order = _completion_order("response_ratio")
     assert sorted(order) == [0, 1, 2]
     assert order.index(2) < order.index(1)
+
+
+def test_size_lanes_policy_runs_large_requests_one_at_a_time():
+    """Two slots: the second long request (at least the average work) waits
+    while the first runs, and the short one behind it passes it."""
+    order = _completion_order("size_lanes", slots=2)
+    assert sorted(order) == [0, 1, 2]
+    assert order.index(2) < order.index(1) and order.index(0) < order.index(1)
