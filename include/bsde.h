@@ -286,6 +286,41 @@ BSDE_API int bsde_set_shard(bsde_ctx* ctx, int rank, int nranks, double* c_dev, 
 /* The block [*i0, *i1) of rank `rank` (host only, no GPU). */
 BSDE_API int bsde_shard_block(int n, int rank, int nranks, int* i0, int* i1);
 
+/* The same sharding with the exchange done on the devices by peer stores,
+ * for GPUs that address each other's memory (NVLink peers of one node, with
+ * peer access enabled or the buffers mapped by the caller).  Every rank owns
+ * a correction buffer of c_len >= 2 * nranks * nb doubles and an array of
+ * nranks uint32 arrival counters, zeroed before the first solve; px gives,
+ * for every rank q, the addresses of q's buffer and counters as this
+ * context's device sees them.  In each iteration, after its block of
+ * corrections is computed (into its own buffer), this rank stores the block
+ * into every other rank's buffer at the same offset and then raises its
+ * counter in their arrays to the iteration's exchange number (stream-ordered
+ * kernels); it then waits on the device until every other rank's counter in
+ * its own array has reached that number, at most wait_ms milliseconds
+ * (0: 1000).  If the bound passes (a rank that failed or never joined) the
+ * solve completes without further waits and returns BSDE_ERR_TIMEOUT; the
+ * context stays usable.  Buffers alternate between two halves from one
+ * exchange to the next, so a rank one exchange ahead never overwrites data
+ * that another still reads.  pushed (optional) is called on the host after
+ * this rank's push has been enqueued and before the wait is, with this
+ * rank's buffer (as bsde_exchange_fn: its return value is ignored unless
+ * nonzero, which fails the solve with BSDE_ERR_EXCHANGE).  The result
+ * equals the unsharded solve bit for bit, as with bsde_set_shard.  The
+ * exchange numbers count on from the previous solves of the context, so
+ * every rank must run the same sequence of solves.  nranks = 1 or
+ * bsde_set_shard(ctx, 0, 1, ...) turns sharding off. */
+#define BSDE_MAX_RANKS 64
+typedef struct {
+  double* c[BSDE_MAX_RANKS];      /* rank q's correction buffer              */
+  uint32_t* flag[BSDE_MAX_RANKS]; /* rank q's arrival counters (nranks each) */
+  size_t c_len;                   /* doubles in each correction buffer       */
+  double wait_ms;                 /* bound of the device wait (0: 1000 ms)   */
+  bsde_exchange_fn pushed;        /* optional host call between push and wait */
+  void* user;                     /* passed back to pushed                   */
+} bsde_peer_exchange;
+BSDE_API int bsde_set_shard_peers(bsde_ctx* ctx, int rank, int nranks, const bsde_peer_exchange* px);
+
 /* Basis size p of the current solve parameters, and the multi-indices in
  * the library's order (p x (d+1) ints, graded, lexicographically descending
  * with the time variate first).  Host-only; needs no GPU. */
@@ -336,8 +371,11 @@ BSDE_API int bsde_eval_price_delta(bsde_ctx* ctx, int q, const double* t, const 
  * in FP64 precision when M >= 256 and the basis tables fit; fewer for small
  * M or large bases); larger problems are rejected with BSDE_ERR_NOMEM
  * before any device work.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  Every call uses the same array
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture, and do not call this entry point on a device after a
+ * cudaDeviceReset of that device in the same process (the array may then
+ * live at another address).  Each call blocks until its work is done.  Every call uses the same array
  * and the array keeps the last call's contents; each call rewrites every
  * scratch word it reads, so nothing needs clearing, but calls that overlap
  * on the GPU (other streams, other host threads) race on the array and must

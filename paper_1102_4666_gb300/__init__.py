@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libbsde_gb300.so")
 
 MAX_D = 16
 MAX_IT = 64
+MAX_RANKS = 64
 
 OK = 0
 ERR_INVALID_ARG = -1
@@ -99,6 +100,12 @@ class bsde_report(ctypes.Structure):
                 "rank": self.rank}
 
 
+class bsde_peer_exchange(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_void_p * MAX_RANKS), ("flag", ctypes.c_void_p * MAX_RANKS),
+                ("c_len", ctypes.c_size_t), ("wait_ms", ctypes.c_double), ("pushed", exchange_fn),
+                ("user", ctypes.c_void_p)]
+
+
 class bsde_server_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_slots", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
                 ("precision", ctypes.c_int), ("policy", ctypes.c_int)]
@@ -132,6 +139,8 @@ _SIGNATURES = {
                                         _dptr, ctypes.c_int]),
     "bsde_set_shard": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_size_t, exchange_fn, ctypes.c_void_p]),
+    "bsde_set_shard_peers": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(bsde_peer_exchange)]),
     "bsde_shard_block": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
     "bsde_basis_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -421,6 +430,34 @@ class Solver:
         self._shard = (cb, xbuf, exchange)  # keep alive while the setting holds
         return self._check(lib().bsde_set_shard(self.h, rank, nranks, xbuf.data_ptr(), xbuf.numel(), cb,
                                                 None))
+
+    def set_shard_peers(self, rank, nranks, bufs, flags, wait_ms=0.0, pushed=None):
+        """Sharding with the exchange done by the devices (bsde_set_shard_peers):
+        bufs[q] / flags[q] are rank q's float64 correction buffer (at least
+        2 * nranks * ceil(n / nranks) values) and uint32/int32 arrival
+        counters (nranks, zeroed), as tensors this device can address;
+        pushed(nb, rank, nranks, stream), if given, runs on the host between
+        this rank's push and its device-side wait."""
+        px = bsde_peer_exchange()
+        for q in range(nranks):
+            px.c[q] = bufs[q].data_ptr()
+            px.flag[q] = flags[q].data_ptr()
+        px.c_len = min(b.numel() for b in bufs)
+        px.wait_ms = wait_ms
+        cb = exchange_fn()
+        if pushed is not None:
+            def _hook(c_dev, nb, rank_, nranks_, stream, user):
+                try:
+                    pushed(nb, rank_, nranks_, stream or 0)
+                    return 0
+                except Exception:
+                    import traceback
+                    traceback.print_exc()
+                    return 1
+            cb = exchange_fn(_hook)
+        px.pushed = cb
+        self._shard = (cb, bufs, flags, px)  # keep alive while the setting holds
+        return self._check(lib().bsde_set_shard_peers(self.h, rank, nranks, ctypes.byref(px)))
 
     def basis_size(self, eta=None, q=None):
         eta = self.cfg["eta"] if eta is None else eta

@@ -240,6 +240,35 @@ int bsde_set_shard(bsde_ctx* c, int rank, int nranks, double* c_dev, size_t c_le
   P.sh_len = nranks > 1 ? c_len : 0;
   P.sh_fn = nranks > 1 ? exchange : nullptr;
   P.sh_user = user;
+  P.sh_peer = false;
+  return BSDE_OK;
+}
+
+int bsde_set_shard_peers(bsde_ctx* c, int rank, int nranks, const bsde_peer_exchange* px) {
+  if (!c) return BSDE_ERR_INVALID_ARG;
+  if (nranks < 1 || nranks > BSDE_MAX_RANKS || rank < 0 || rank >= nranks)
+    return fail(c, BSDE_ERR_INVALID_ARG, "set_shard_peers: rank out of range");
+  if (nranks == 1) return bsde_set_shard(c, 0, 1, nullptr, 0, nullptr, nullptr);
+  if (!px) return fail(c, BSDE_ERR_INVALID_ARG, "set_shard_peers: NULL peer table");
+  for (int q = 0; q < nranks; ++q)
+    if (!px->c[q] || !px->flag[q])
+      return fail(c, BSDE_ERR_INVALID_ARG, "set_shard_peers: missing buffer or counters of a rank");
+  if (!(px->wait_ms >= 0.0) || px->wait_ms > 3.6e6)
+    return fail(c, BSDE_ERR_INVALID_ARG, "set_shard_peers: wait_ms out of range");
+  Problem& P = c->prob;
+  P.destroy_graph();
+  P.sh_rank = rank;
+  P.sh_n = nranks;
+  P.sh_buf = px->c[rank];
+  P.sh_len = px->c_len;
+  P.sh_fn = px->pushed;
+  P.sh_user = px->user;
+  P.sh_peer = true;
+  P.sh_wait_ms = px->wait_ms > 0.0 ? px->wait_ms : 1000.0;
+  for (int q = 0; q < BSDE_RANKS_MAX; ++q) {
+    P.sh_pp.c[q] = q < nranks ? px->c[q] : nullptr;
+    P.sh_pp.flag[q] = q < nranks ? px->flag[q] : nullptr;
+  }
   return BSDE_OK;
 }
 

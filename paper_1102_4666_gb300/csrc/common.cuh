@@ -8,6 +8,14 @@
 
 #define BSDE_DMAX 16
 #define BSDE_NNZ_MAX 8  // active variates per basis function
+#define BSDE_RANKS_MAX 64  // ranks of a point-sharded solve (BSDE_MAX_RANKS of the C ABI)
+
+// device addresses, as this device sees them, of every rank's correction
+// buffer and arrival-counter array (peer exchange of a sharded solve)
+struct PeerPtrs {
+  double* c[BSDE_RANKS_MAX];
+  uint32_t* flag[BSDE_RANKS_MAX];
+};
 
 // Philox4x32-10 counter tags (top byte of the fourth counter word)
 #define TAG_PTS 1u
@@ -237,3 +245,12 @@ void launch_qr_solve(const ProblemDev& P, cudaStream_t st);
 void launch_inverse(const ProblemDev& P, int nb, cudaStream_t st);
 void launch_inv_gemv(const ProblemDev& P, const double* b, double* x, int accumulate, cudaStream_t st);
 int paths_supported_d(int d);
+// peer exchange of a sharded solve: push this rank's block [i0, i0 + count)
+// of `mine` into every other rank's buffer (at region_off) and raise their
+// counters to `epoch`; then wait, at most wait_ms, for the others' counters
+// in `flags` (ST_TIMEOUT in status when the bound passes)
+cudaError_t launch_exchange_peers(const double* mine, int i0, int count, int rank, int nranks,
+                                  const PeerPtrs& pp, size_t region_off, uint32_t epoch,
+                                  cudaStream_t st);
+cudaError_t launch_exchange_wait(const uint32_t* flags, int rank, int nranks, uint32_t epoch,
+                                 double wait_ms, int* status, cudaStream_t st);

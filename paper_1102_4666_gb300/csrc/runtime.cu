@@ -526,8 +526,10 @@ int Problem::prepare(const bsde_solve_params& prm, Allocator& al, size_t budget,
   dev.shard_n = 0;
   if (sh_n > 1) {
     const int nb = (n + sh_n - 1) / sh_n;
-    if (!sh_buf || sh_len < (size_t)nb * sh_n) {
-      err = "solve: the shard exchange buffer holds fewer than nranks * ceil(n / nranks) values";
+    const size_t need_len = (size_t)nb * sh_n * (sh_peer ? 2 : 1);
+    if (!sh_buf || sh_len < need_len) {
+      err = sh_peer ? "solve: the peer exchange buffers hold fewer than 2 * nranks * ceil(n / nranks) values"
+                    : "solve: the shard exchange buffer holds fewer than nranks * ceil(n / nranks) values";
       return BSDE_ERR_INVALID_ARG;
     }
     int i0, i1;
@@ -629,6 +631,14 @@ int Problem::enqueue_gram(int k, cudaStream_t st) {
 int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t st,
                                cudaEvent_t* ev, int slot) {
   const bool rec = ev != nullptr;
+  // peer exchange: this iteration's corrections live in the half of the
+  // buffers that belongs to its exchange number
+  const uint32_t epoch = sh_epoch + 1;
+  size_t region_off = 0;
+  if (sh_n > 1 && sh_peer) {
+    region_off = (size_t)(epoch & 1u) * (size_t)sh_n * (size_t)((shape.n + sh_n - 1) / sh_n);
+    dev.c = sh_buf + region_off;
+  }
   const uint32_t kp = grid.resample ? (uint32_t)k : 0u;
   launch_points(model, grid, dev, kp, st);
   launch_basis(model, grid, dev, false, st);  // FP64 B for the refit (no TF32 split)
@@ -650,10 +660,32 @@ int Problem::enqueue_iteration(const bsde_solve_params& prm, int k, cudaStream_t
       return BSDE_ERR_CUDA;
     }
     const int nb = (shape.n + sh_n - 1) / sh_n;
-    const int rc = sh_fn(sh_buf, nb, sh_rank, sh_n, (void*)st, sh_user);
-    if (rc != 0) {
-      err = "solve: the exchange hook failed (status " + std::to_string(rc) + ")";
-      return BSDE_ERR_EXCHANGE;
+    if (sh_peer) {
+      e = launch_exchange_peers(dev.c, dev.shard_i0, dev.shard_n, sh_rank, sh_n, sh_pp, region_off,
+                                epoch, st);
+      if (e != cudaSuccess) {
+        err = std::string("exchange launch failed: ") + cudaGetErrorString(e);
+        return BSDE_ERR_CUDA;
+      }
+      if (sh_fn) {
+        const int rc = sh_fn(dev.c, nb, sh_rank, sh_n, (void*)st, sh_user);
+        if (rc != 0) {
+          err = "solve: the exchange hook failed (status " + std::to_string(rc) + ")";
+          return BSDE_ERR_EXCHANGE;
+        }
+      }
+      e = launch_exchange_wait(sh_pp.flag[sh_rank], sh_rank, sh_n, epoch, sh_wait_ms, dev.status, st);
+      if (e != cudaSuccess) {
+        err = std::string("exchange launch failed: ") + cudaGetErrorString(e);
+        return BSDE_ERR_CUDA;
+      }
+      sh_epoch = epoch;
+    } else {
+      const int rc = sh_fn(sh_buf, nb, sh_rank, sh_n, (void*)st, sh_user);
+      if (rc != 0) {
+        err = "solve: the exchange hook failed (status " + std::to_string(rc) + ")";
+        return BSDE_ERR_EXCHANGE;
+      }
     }
   }
   if (rec) record(ev[2], st);

@@ -55,6 +55,12 @@ class Problem {
   size_t sh_len = 0;
   bsde_exchange_fn sh_fn = nullptr;
   void* sh_user = nullptr;
+  // peer exchange (bsde_set_shard_peers): every rank's buffer and counters,
+  // the wait bound and the exchange number of the last exchange
+  bool sh_peer = false;
+  PeerPtrs sh_pp;
+  double sh_wait_ms = 1000.0;
+  uint32_t sh_epoch = 0;
 
   ~Problem();
   // validate params, build the basis, (re)allocate device memory; BSDE_OK or an error

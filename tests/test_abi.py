@@ -54,6 +54,7 @@ int main(void) {
   P(bsde_server_opts) O(bsde_server_opts, precision) O(bsde_server_opts, policy)
   P(bsde_request) O(bsde_request, params) O(bsde_request, hi) O(bsde_request, n)
   P(bsde_server_stats) O(bsde_server_stats, path_steps_per_s)
+  P(bsde_peer_exchange) O(bsde_peer_exchange, flag) O(bsde_peer_exchange, c_len) O(bsde_peer_exchange, wait_ms) O(bsde_peer_exchange, pushed) O(bsde_peer_exchange, user)
   return 0;
 }
 """

@@ -136,3 +136,88 @@ def test_torch_distributed_exchange_on_the_solve_stream(G, tmp_path):
         assert torch.equal(xbuf.cpu(), torch.arange(10, dtype=torch.float64) * 2.0)
     finally:
         dist.destroy_process_group()
+
+
+def _peer_solve(G, cfg, prec, nranks):
+    """R ranks as host threads sharing one GPU, exchanging by peer stores
+    into each other's buffers.  The pushed hook holds every rank at a host
+    barrier until all ranks' pushes and counters have completed, so each
+    device-side wait finds its counters already raised: no kernel waits for
+    another kernel."""
+    import torch
+    n = cfg["n"]
+    nb = (n + nranks - 1) // nranks
+    bufs = [torch.zeros(2 * nranks * nb, dtype=torch.float64, device="cuda") for _ in range(nranks)]
+    flags = [torch.zeros(nranks, dtype=torch.int32, device="cuda") for _ in range(nranks)]
+    barrier = threading.Barrier(nranks, timeout=120)
+    out = [None] * nranks
+    errs = []
+
+    def pushed(nb_, rank, R, stream):
+        torch.cuda.ExternalStream(int(stream)).synchronize()
+        barrier.wait()
+
+    def run(rank):
+        try:
+            torch.cuda.set_device(0)
+            s = G.Solver(cfg, precision=prec)
+            s.set_shard_peers(rank, nranks, bufs, flags, wait_ms=2000.0, pushed=pushed)
+            rep = s.solve(use_graph=1)
+            out[rank] = (rep.price, s.coeffs(), rep.status)
+            s.close()
+        except Exception as e:  # pragma: no cover - reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=run, args=(r,)) for r in range(nranks)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=600)
+    assert not errs, errs
+    return out, flags
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("nranks", [2, 3])
+def test_peer_exchange_equals_unsharded(G, prec, nranks):
+    cfg = workloads.config("c4", n=301, M=96, N=6, eta=2, K_it=3, **{"lambda": 1.0})
+    s = G.Solver(cfg, precision=prec)
+    ref = s.solve()
+    a_ref = s.coeffs()
+    s.close()
+    out, flags = _peer_solve(G, cfg, prec, nranks)
+    for price, alpha, status in out:
+        assert status == G.OK
+        assert np.array_equal(alpha, a_ref) and price == ref.price
+    # every rank raised its counter at every other rank once per iteration
+    for r in range(nranks):
+        f = flags[r].cpu().numpy()
+        assert all(f[q] == cfg["K_it"] for q in range(nranks) if q != r)
+
+
+def test_peer_exchange_wait_runs_out_when_a_rank_never_joins(G):
+    """Rank 0 of 2 alone: nobody raises its counter for rank 1, so its
+    device-side wait gives up after wait_ms; the solve returns
+    BSDE_ERR_TIMEOUT without waiting again in later iterations, and the
+    context then solves unsharded as before."""
+    import time
+    import torch
+    cfg = workloads.config("c4", n=200, M=64, N=4, eta=2, K_it=3, **{"lambda": 1.0})
+    s = G.Solver(cfg, precision="mixed")
+    ref = s.solve()
+    nb = 100
+    bufs = [torch.zeros(4 * nb, dtype=torch.float64, device="cuda") for _ in range(2)]
+    flags = [torch.zeros(2, dtype=torch.int32, device="cuda") for _ in range(2)]
+    s.set_shard_peers(0, 2, bufs, flags, wait_ms=50.0)
+    t0 = time.monotonic()
+    rep = s.solve(check=False)
+    el = time.monotonic() - t0
+    assert rep.status == G.ERR_TIMEOUT
+    assert "bounded device wait" in G.lib().bsde_last_error(s.h).decode()
+    assert el < 10.0
+    # rank 0 did push to rank 1 and raise its counter there, once per iteration
+    assert int(flags[1][0].item()) == cfg["K_it"]
+    s.set_shard(0, 1)
+    again = s.solve()
+    assert again.status == G.OK and again.price == ref.price
+    s.close()
