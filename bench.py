@@ -331,12 +331,16 @@ def run_serving_fp64_measured(n_requests=24, seed=17, load=0.7, m_div=8):
             "mixed_4_slots": run_serving(reqs, arr, precision="mixed", slots=4, policy="fifo")}
 
 
-def run_serving_suite(n_requests, seed=7, load=0.8):
+def run_serving_suite(n_requests, seed=7, load=0.8, compare_requests=300):
     """One seeded request mix and one arrival stream (rate: `load` times the
-    16-slot capacity), served by the continuous-batching server with 16 or 4
-    slots and the FIFO, shortest-first and response-ratio admission
-    policies, one request at a time (mixed precision), and the modeled
-    one-at-a-time FP64 comparator."""
+    16-slot capacity).  The whole stream (n_requests; the configured mix has
+    2000) is served by the size-lane continuous-batching server (16 slots)
+    and one request at a time (mixed precision).  Its first compare_requests
+    requests, with the same arrival times, are served by every policy and
+    slot count for comparison: FIFO with 16 or 4 slots, shortest-first and
+    response-ratio with 4, size lanes with 16 and one at a time.  Besides:
+    the modeled one-at-a-time FP64 comparator on the whole stream and a
+    measured one on a smaller mix."""
     reqs = workloads.serving_mix(n_requests, seed=seed)
     mean_steps = sum(workloads.path_steps(r) for r in reqs) / len(reqs)
     cap = serving_capacity(reqs)
@@ -344,15 +348,20 @@ def run_serving_suite(n_requests, seed=7, load=0.8):
     arr = arrival_times(len(reqs), rate, seed)
     out = {"arrival_rate_hz": rate, "calibrated_capacity_path_steps_per_s": cap, "load": load,
            "requests": len(reqs)}
-    out["fifo_16"] = run_serving(reqs, arr, slots=16, policy="fifo")
-    out["fifo_4"] = run_serving(reqs, arr, slots=4, policy="fifo")
-    out["shortest_first_4"] = run_serving(reqs, arr, slots=4, policy="shortest")
-    out["response_ratio_4"] = run_serving(reqs, arr, slots=4, policy="response_ratio")
-    out["response_ratio_16"] = run_serving(reqs, arr, slots=16, policy="response_ratio")
     out["size_lanes_16"] = run_serving(reqs, arr, slots=16, policy="size_lanes")
-    out["size_lanes_4"] = run_serving(reqs, arr, slots=4, policy="size_lanes")
     out["one_at_a_time_mixed"] = run_serving(reqs, arr, slots=1, policy="fifo")
     out["one_at_a_time_fp64"] = fp64_sequential_model(reqs, arr)
+    nc = min(compare_requests, len(reqs))
+    if nc < len(reqs):
+        cmp_ = {"requests": nc, "note": "the first %d requests of the same stream and arrival times" % nc}
+        rq, ar = reqs[:nc], arr[:nc]
+        cmp_["size_lanes_16"] = run_serving(rq, ar, slots=16, policy="size_lanes")
+        cmp_["one_at_a_time_mixed"] = run_serving(rq, ar, slots=1, policy="fifo")
+        cmp_["fifo_16"] = run_serving(rq, ar, slots=16, policy="fifo")
+        cmp_["fifo_4"] = run_serving(rq, ar, slots=4, policy="fifo")
+        cmp_["shortest_first_4"] = run_serving(rq, ar, slots=4, policy="shortest")
+        cmp_["response_ratio_4"] = run_serving(rq, ar, slots=4, policy="response_ratio")
+        out["policies_on_a_prefix"] = cmp_
     out["fp64_comparator_measured"] = run_serving_fp64_measured()
     return out
 
@@ -582,8 +591,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--case", default="bench", choices=["bench", "profile", "profile_tree"])
     ap.add_argument("--no-others", action="store_true", help="skip the other configured workloads")
-    ap.add_argument("--serving-requests", type=int, default=100,
-                    help="requests of the Poisson serving mix (0: skip; 2000: the full mix)")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests of the Poisson serving mix (0: skip; default: the configured 2000)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--shard", action="store_true",
                     help="under torchrun: shard the points of one problem over the ranks (strong "

@@ -107,9 +107,10 @@ __device__ __forceinline__ uint4 philox_rk(const Args<R, D>& a, uint32_t c0, uin
 }
 
 // Philox4x32-10 for a stream of counters (c0, c1, c2, c3) of which only c0
-// varies: the parts of rounds 1 and 2 that depend on c1, c2 and c3 alone are
-// computed once (PhiloxFixed) and the stream's blocks take 3 fewer wide
-// multiplies and xors each.  Same outputs as philox_rk.
+// varies along a path: the parts of rounds 1 and 2 that depend on c1 = m
+// (the path) and c2 = i are computed once per path (PhiloxFixed); the parts
+// that depend on c0, c2 and c3 only are shared by the paths of a point
+// (philox_prep, below).
 struct PhiloxFixed {
   uint32_t n0;    // round 1: hi(c2 M1) ^ c1 ^ k0
   uint32_t lo1;   // round 1: lo(c2 M1)
@@ -132,26 +133,47 @@ __device__ __forceinline__ PhiloxFixed philox_fix(const Args<R, D>& a, uint32_t 
   return f;
 }
 
+// The normals' blocks (b, m, i, tag) of all the paths of one point share
+// (b, i, tag): rounds 1-3 of Philox4x32-10 contain products and xors of those
+// words alone, which philox_prep computes once per block index and point
+// (a table in shared memory), leaving each path one wide multiply and three
+// xors for rounds 1-3 besides its own PhiloxFixed words:
+//   round 1: (n0, lo(i M1), hi(b M0) ^ tag ^ k1_0, lo(b M0))
+//   round 2: (hi(R1_2 M1) ^ lo(i M1) ^ k0_1, lo(R1_2 M1), hiA ^ V, loA),
+//            V = lo(b M0) ^ k1_1
+//   round 3: (hi(R2_2 M1) ^ W, lo(R2_2 M1), U1 ^ loA, U3),
+//            W = lo(R1_2 M1) ^ k0_2, U1 = hi(R2_0 M0) ^ k1_2, U3 = lo(R2_0 M0)
+// (R1_2 = round 1's word 2, R2_* = round 2's words); table entry (V, W, U1, U3).
 template <typename R, int D>
-__device__ __forceinline__ uint4 philox_var(const Args<R, D>& a, const PhiloxFixed& f,
-                                            uint32_t c0) {
-  // round 1
-  const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u;
-  uint32_t c2 = (uint32_t)(p0 >> 32) ^ f.c3k;
-  uint32_t c3 = (uint32_t)p0;
-  // round 2 (c0 = f.n0, c1 = f.lo1)
-  const uint64_t p1 = (uint64_t)c2 * 0xCD9E8D57u;
-  c0 = (uint32_t)(p1 >> 32) ^ f.lo1 ^ a.rk0[1];
-  c2 = f.hiA ^ c3 ^ a.rk1[1];
-  uint32_t c1 = (uint32_t)p1;
-  c3 = f.loA;
+__device__ __forceinline__ uint4 philox_prep(const Args<R, D>& a, uint32_t b, uint32_t c2,
+                                             uint32_t c3) {
+  const uint64_t p0 = (uint64_t)b * 0xD2511F53u;
+  const uint32_t r1_2 = (uint32_t)(p0 >> 32) ^ c3 ^ a.rk1[0];
+  const uint32_t r1_3 = (uint32_t)p0;
+  const uint32_t r1_1 = (uint32_t)((uint64_t)c2 * 0xCD9E8D57u);
+  const uint64_t p1 = (uint64_t)r1_2 * 0xCD9E8D57u;
+  const uint32_t r2_0 = (uint32_t)(p1 >> 32) ^ r1_1 ^ a.rk0[1];
+  const uint32_t r2_1 = (uint32_t)p1;
+  const uint64_t q0 = (uint64_t)r2_0 * 0xD2511F53u;
+  return make_uint4(r1_3 ^ a.rk1[1], r2_1 ^ a.rk0[2], (uint32_t)(q0 >> 32) ^ a.rk1[2], (uint32_t)q0);
+}
+
+// the block (b, m, i, tag) of a path from its PhiloxFixed words and the
+// table entry of philox_prep for b: the same outputs as philox_rk
+template <typename R, int D>
+__device__ __forceinline__ uint4 philox_tab(const Args<R, D>& a, const PhiloxFixed& f, uint4 pre) {
+  const uint64_t q1 = (uint64_t)(f.hiA ^ pre.x) * 0xCD9E8D57u;
+  uint32_t c0 = (uint32_t)(q1 >> 32) ^ pre.y;
+  uint32_t c1 = (uint32_t)q1;
+  uint32_t c2 = pre.z ^ f.loA;
+  uint32_t c3 = pre.w;
 #pragma unroll
-  for (int r = 2; r < 10; ++r) {
+  for (int r = 3; r < 10; ++r) {
     const uint64_t q0 = (uint64_t)c0 * 0xD2511F53u;
-    const uint64_t q1 = (uint64_t)c2 * 0xCD9E8D57u;
-    const uint32_t n0 = (uint32_t)(q1 >> 32) ^ c1 ^ a.rk0[r];
+    const uint64_t qq = (uint64_t)c2 * 0xCD9E8D57u;
+    const uint32_t n0 = (uint32_t)(qq >> 32) ^ c1 ^ a.rk0[r];
     const uint32_t n2 = (uint32_t)(q0 >> 32) ^ c3 ^ a.rk1[r];
-    c1 = (uint32_t)q1;
+    c1 = (uint32_t)qq;
     c3 = (uint32_t)q0;
     c0 = n0;
     c2 = n2;
@@ -546,6 +568,42 @@ __device__ __forceinline__ void eval_tree(const Args<R, D>& a, const R* __restri
   gen = r.b + R(0.5) * ((R(1) - a.rho) * r.dg + a.rho * r.ss);
 }
 
+// One Euler step of every asset of X (in place), with the sqrt(h)-scaled
+// normals z[gs D .. gs D + D) of a group of G steps and the volatility row
+// tabs of the step: X_j += h (r - delta_j) + sigma_j (y_j - h sigma_j / 2),
+// y = sqrt(h) (L Z)_j, sigma_j at (t_s, X_s).  The main loop and the
+// reconstruction of the states around the random time both call it, so the
+// two compute the same numbers.
+template <int VK, bool CC, int G, typename R, int D>
+__device__ __forceinline__ void euler_step(const Args<R, D>& a, const R* tabs, const R (&z)[G * D],
+                                           int gs, R nhh, R h, R (&X)[D]) {
+  R pre = 0;  // running sum of the constant-correlation factor
+  float4 q4;  // (A_j, B_j, A_j+1, B_j+1) of the FP32 tanh families
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    // correlated increment y = sqrt(h) (L Z)_j
+    R y;
+    if constexpr (CC) {
+      y = a.Ld[j] * z[gs * D + j] + pre;
+      pre += a.Lc[j] * z[gs * D + j];
+    } else {
+      y = 0;
+#pragma unroll
+      for (int q = 0; q <= j; ++q) y += a.L[j][q] * z[gs * D + q];
+    }
+    R sig;
+    if constexpr ((VK == VK_TANH || VK == VK_TANH_ABS) && sizeof(R) == 4) {
+      if ((j & 1) == 0) q4 = reinterpret_cast<const float4*>(tabs)[j >> 1];
+      const R r = tanh_r<VK == VK_TANH_ABS>(a, j, X[j]);
+      sig = (j & 1) ? (q4.z + q4.w * r) : (q4.x + q4.y * r);
+    } else {
+      sig = sigma_j<VK>(a, tabs, j, X[j]);
+    }
+    // X + (r - delta_j - sigma^2/2) h + sigma y = X + h rd_j + sigma (y - h sigma / 2)
+    X[j] = sig * (nhh * sig + y) + (h * a.rd[j] + X[j]);
+  }
+}
+
 template <int VK, int EV, bool CC, typename R, int D>
 __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R, D> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -577,6 +635,8 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     off = (off + 15) & ~(size_t)15;
   }
   double* red = reinterpret_cast<double*>(smem_raw + off);          // 32
+  // rounds 1-3 of the normals' Philox blocks (philox_prep), per block index
+  uint4* s_ph = reinterpret_cast<uint4*>(smem_raw + off + 32 * sizeof(double));
 
   const R ti = (R)a.pt[i];
   R x0[D];
@@ -612,12 +672,15 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     }
   }
   for (int q = tid; q < DP * DP; q += tpb) s_cp[q] = (&a.Cp[0][0])[q];
-  __syncthreads();
-
   const uint32_t tagU = (TAG_U << 24) | a.k, tagZ = (TAG_Z << 24) | a.k, tagB = (TAG_B << 24) | a.k;
   constexpr int G = 4 / gcd_c(D, 4);  // steps per group: G*D normals = whole Philox blocks
   constexpr int NB = G * D / 4;
   constexpr int NBB = (D + 3) / 4;
+  {
+    const int nblk = (a.N + G - 1) / G * NB;
+    for (int b = tid; b < nblk; b += tpb) s_ph[b] = philox_prep(a, (uint32_t)b, (uint32_t)i, tagZ);
+  }
+  __syncthreads();
   const int ppc = tpb * a.ppt;
   double acc = 0.0;
 
@@ -642,13 +705,14 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const int sstar = (int)(wN >> 32);
     const R theta = uniform_frac<R>((uint32_t)wN);
 
-    // state, and at the step s* that contains tau: X before and after it
-    R X[D], Xs[D], Xn[D];
+    // state, and at the start of the group of G steps that contains s*
+    // (the step that contains tau) a copy of it
+    const int g_hit = sstar - sstar % G;
+    R X[D], Xg[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       X[j] = x0[j];
-      Xs[j] = x0[j];
-      Xn[j] = x0[j];
+      Xg[j] = x0[j];
     }
     const R nhh = R(-0.5) * h;
     const PhiloxFixed pz = philox_fix(a, (uint32_t)m, (uint32_t)i, tagZ);
@@ -657,60 +721,60 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
       const uint32_t blk0 = (uint32_t)(s0 / G) * (uint32_t)NB;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        const uint4 o = philox_var(a, pz, blk0 + b);
+        const uint4 o = philox_tab(a, pz, s_ph[blk0 + b]);
         Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1], bmk);
         Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3], bmk);
+      }
+      const bool hit = (s0 == g_hit);
+      // the vote is over the lanes that reach this group together; a lane
+      // with hit set always votes for itself, so its copy is never skipped.
+      // Without the vote the copy is D predicated moves per group; the vote
+      // and its branch pay off from d = 3 on, except next to the dense
+      // evaluations of d >= 6 (the degree-3 loops at any d), whose registers
+      // leave no room for it.
+      constexpr bool VOTE = D >= 3 && EV != EV_DENSE3 && !(EV >= EV_TREE4 && D >= 6);
+      const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
+      if (any_hit) {
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+          if (hit) Xg[j] = X[j];
       }
 #pragma unroll
       for (int gs = 0; gs < G; ++gs) {
         const int s = s0 + gs;
-        if (s < a.N) {
-          const R* tabs = tab + s * a.tab_stride;
-          const bool hit = (s == sstar);
-          // the vote is over the lanes that reach this step together; a lane
-          // with hit set always votes for itself, so its copies are never
-          // skipped.  Without the vote the copies are 2 D predicated moves per
-          // step; the vote and its branch pay off from d = 3 on, except next
-          // to the dense evaluations of d >= 6 (the degree-3 loops at any d),
-          // whose registers leave no room for it.
-          constexpr bool VOTE = D >= 3 && EV != EV_DENSE3 && !(EV >= EV_TREE4 && D >= 6);
-          const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
-          if (any_hit) {
+        if (s < a.N) euler_step<VK, CC, G>(a, tab + s * a.tab_stride, z, gs, nhh, h, X);
+      }
+    }
+
+    // X before and after step s*: the group's normals drawn again (the same
+    // counters) and its steps taken again from the copy at the group start
+    R Xs[D], Xn[D];
+    {
+      R zr[G * D];
+      const uint32_t blk0 = (uint32_t)(g_hit / G) * (uint32_t)NB;
 #pragma unroll
-            for (int j = 0; j < D; ++j)
-              if (hit) Xs[j] = X[j];
-          }
-          R pre = 0;  // running sum of the constant-correlation factor
-          float4 q4;  // (A_j, B_j, A_j+1, B_j+1) of the FP32 tanh families
+      for (int b = 0; b < NB; ++b) {
+        const uint4 o = philox_tab(a, pz, s_ph[blk0 + b]);
+        Math<R>::box_muller(o.x, o.y, zr[4 * b + 0], zr[4 * b + 1], bmk);
+        Math<R>::box_muller(o.z, o.w, zr[4 * b + 2], zr[4 * b + 3], bmk);
+      }
 #pragma unroll
-          for (int j = 0; j < D; ++j) {
-            // correlated increment y = sqrt(h) (L Z)_j
-            R y;
-            if constexpr (CC) {
-              y = a.Ld[j] * z[gs * D + j] + pre;
-              pre += a.Lc[j] * z[gs * D + j];
-            } else {
-              y = 0;
+      for (int j = 0; j < D; ++j) Xs[j] = Xg[j];
 #pragma unroll
-              for (int q = 0; q <= j; ++q) y += a.L[j][q] * z[gs * D + q];
-            }
-            R sig;
-            if constexpr ((VK == VK_TANH || VK == VK_TANH_ABS) && sizeof(R) == 4) {
-              if ((j & 1) == 0) q4 = reinterpret_cast<const float4*>(tabs)[j >> 1];
-              const R r = tanh_r<VK == VK_TANH_ABS>(a, j, X[j]);
-              sig = (j & 1) ? (q4.z + q4.w * r) : (q4.x + q4.y * r);
-            } else {
-              sig = sigma_j<VK>(a, tabs, j, X[j]);
-            }
-            // X + (r - delta_j - sigma^2/2) h + sigma y = X + h rd_j + sigma (y - h sigma / 2)
-            X[j] = sig * (nhh * sig + y) + (h * a.rd[j] + X[j]);
-          }
-          if (any_hit) {
+      for (int gs = 0; gs < G; ++gs) {
+        // steps past s* (and past the last step) are not needed; their table
+        // row is clamped so that every read stays in the table
+        const int s = g_hit + gs;
+        const int row = s < a.N ? s : a.N - 1;
+        if (gs > 0) {
 #pragma unroll
-            for (int j = 0; j < D; ++j)
-              if (hit) Xn[j] = X[j];
-          }
+          for (int j = 0; j < D; ++j)
+            if (s <= sstar) Xs[j] = Xg[j];
         }
+        euler_step<VK, CC, G>(a, tab + row * a.tab_stride, zr, gs, nhh, h, Xg);
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+          if (s == sstar) Xn[j] = Xg[j];
       }
     }
 
@@ -835,6 +899,11 @@ inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bo
     off = (off + 15) & ~(size_t)15;
   }
   off += 32 * sizeof(double);
+  // the Philox table of the normals: 16 bytes per block, ceil(N / G) G d / 4
+  // blocks with G = 4 / gcd(d, 4) steps per group
+  const int gcd = (d % 4 == 0) ? 4 : (d % 2 == 0) ? 2 : 1;
+  const int G = 4 / gcd, NB = G * d / 4;
+  off += (size_t)((N + G - 1) / G) * NB * 16;
   return off;
 }
 
