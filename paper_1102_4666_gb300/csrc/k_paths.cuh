@@ -705,14 +705,30 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const int sstar = (int)(wN >> 32);
     const R theta = uniform_frac<R>((uint32_t)wN);
 
-    // state, and at the start of the group of G steps that contains s*
-    // (the step that contains tau) a copy of it
-    const int g_hit = sstar - sstar % G;
-    R X[D], Xg[D];
+    // The step s* that contains tau needs the states before and after it.
+    // The vote below is over the lanes that reach a copy together; a lane
+    // whose copy is due always votes for itself, so it is never skipped.
+    // Without the vote a copy is D predicated moves; the vote and its branch
+    // pay off from d = 3 on, except next to the dense evaluations of d >= 6
+    // (the degree-3 loops at any d), whose registers leave no room for it.
+    constexpr bool VOTE = D >= 3 && EV != EV_DENSE3 && !(EV >= EV_TREE4 && D >= 6);
+    // Where the copies go behind a vote (FP32 paths), the state is copied
+    // once per group of G steps instead, at the start of the group that
+    // contains s*, and the group's steps are taken again after the loop (its
+    // normals drawn again from the same counters): measured 38.7 -> 37.7 ms
+    // per d = 5 degree-4 solve.  Elsewhere the copies before and after every
+    // step are cheaper than that second pass (d = 3 and 6 with N = 10: 2.30
+    // -> 2.46 and 11.10 -> 11.75 ms per solve; d = 10 with N = 100 even).
+    // Same results either way (the same function takes each step).
+    constexpr bool REBUILD = sizeof(R) == 4 && VOTE;
+    const int g_hit = sstar - sstar % G;  // first step of the group that contains s*
+    R X[D], Xg[D], Xs[D], Xn[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       X[j] = x0[j];
       Xg[j] = x0[j];
+      Xs[j] = x0[j];
+      Xn[j] = x0[j];
     }
     const R nhh = R(-0.5) * h;
     const PhiloxFixed pz = philox_fix(a, (uint32_t)m, (uint32_t)i, tagZ);
@@ -725,31 +741,43 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
         Math<R>::box_muller(o.x, o.y, z[4 * b + 0], z[4 * b + 1], bmk);
         Math<R>::box_muller(o.z, o.w, z[4 * b + 2], z[4 * b + 3], bmk);
       }
-      const bool hit = (s0 == g_hit);
-      // the vote is over the lanes that reach this group together; a lane
-      // with hit set always votes for itself, so its copy is never skipped.
-      // Without the vote the copy is D predicated moves per group; the vote
-      // and its branch pay off from d = 3 on, except next to the dense
-      // evaluations of d >= 6 (the degree-3 loops at any d), whose registers
-      // leave no room for it.
-      constexpr bool VOTE = D >= 3 && EV != EV_DENSE3 && !(EV >= EV_TREE4 && D >= 6);
-      const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
-      if (any_hit) {
+      if constexpr (REBUILD) {
+        const bool hit = (s0 == g_hit);
+        const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
+        if (any_hit) {
 #pragma unroll
-        for (int j = 0; j < D; ++j)
-          if (hit) Xg[j] = X[j];
+          for (int j = 0; j < D; ++j)
+            if (hit) Xg[j] = X[j];
+        }
       }
 #pragma unroll
       for (int gs = 0; gs < G; ++gs) {
         const int s = s0 + gs;
-        if (s < a.N) euler_step<VK, CC, G>(a, tab + s * a.tab_stride, z, gs, nhh, h, X);
+        if (s < a.N) {
+          if constexpr (REBUILD) {
+            euler_step<VK, CC, G>(a, tab + s * a.tab_stride, z, gs, nhh, h, X);
+          } else {
+            const bool hit = (s == sstar);
+            const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
+            if (any_hit) {
+#pragma unroll
+              for (int j = 0; j < D; ++j)
+                if (hit) Xs[j] = X[j];
+            }
+            euler_step<VK, CC, G>(a, tab + s * a.tab_stride, z, gs, nhh, h, X);
+            if (any_hit) {
+#pragma unroll
+              for (int j = 0; j < D; ++j)
+                if (hit) Xn[j] = X[j];
+            }
+          }
+        }
       }
     }
 
-    // X before and after step s*: the group's normals drawn again (the same
-    // counters) and its steps taken again from the copy at the group start
-    R Xs[D], Xn[D];
-    {
+    if constexpr (REBUILD) {
+      // X before and after step s*: the group's normals drawn again (the
+      // same counters) and its steps taken again from the copy at its start
       R zr[G * D];
       const uint32_t blk0 = (uint32_t)(g_hit / G) * (uint32_t)NB;
 #pragma unroll

@@ -295,7 +295,8 @@ _FULL_SIZE = [(0, shape) for shape in __import__(
 def test_full_size_c4_sampled_points(G, ev, shape):
     """c4 at its full size (n=4000, M=4000, N=100, p=364), one mixed
     iteration in each launch configuration bench.py can time (threads per
-    CTA x paths per thread); the oracle recomputes c_i at a sample of points."""
+    CTA x paths per thread); the oracle recomputes c_i at the 256 points
+    i = 0, 15, 30, ... (1e8 path-steps of FP64 oracle work per case)."""
     cfg = workloads.config("c4")
     nu = O.multi_index_set(11, 3)
     a0 = _alpha(cfg, nu, scale=1.0)
@@ -303,7 +304,8 @@ def test_full_size_c4_sampled_points(G, ev, shape):
     kw = {} if shape is None else {"paths_tpb": shape[0], "paths_ppt": shape[1]}
     t, x, c, a1 = s.iterate(5, a0, eval_mode=ev, **kw)
     s.close()
-    idx = np.arange(0, 4000, 500)
+    # the 256-point subset i = 0, 15, 30, ... of the d = 10 configuration
+    idx = np.arange(0, 15 * 256, 15)
     co = O.correction(cfg, nu, a0, 5, idx, t[idx], x[:, idx], nthreads=NTH)
     sc = _scale(cfg, nu, a0, t, x)
     assert np.max(np.abs(c[idx] - co)) < MIXED_C_TOL * sc

@@ -221,3 +221,21 @@ def test_peer_exchange_wait_runs_out_when_a_rank_never_joins(G):
     again = s.solve()
     assert again.status == G.OK and again.price == ref.price
     s.close()
+
+
+def test_more_ranks_than_points_per_block(G):
+    """Seven ranks over six points: nb = 1, and the last rank's block is
+    empty (it launches no path kernel and sends nothing); the result is still
+    the unsharded one bit for bit, with either exchange."""
+    cfg = workloads.make(d=1, T=1.0, r=0.02, K=100.0, S0=100.0, vol={"kind": "const", "a": 0.2}, rho=0.0,
+                         lam=0.0, n=6, M=64, N=4, eta=1, K_it=2, seed=21)
+    s = G.Solver(cfg, precision="fp64")
+    ref = s.solve()
+    a_ref = s.coeffs()
+    s.close()
+    assert G.shard_block(6, 6, 7) == (6, 6)
+    for price, delta, alpha, status in _sharded_solve(G, cfg, "fp64", 7):
+        assert status == G.OK and np.array_equal(alpha, a_ref) and price == ref.price
+    out, _ = _peer_solve(G, cfg, "fp64", 7)
+    for price, alpha, status in out:
+        assert status == G.OK and np.array_equal(alpha, a_ref) and price == ref.price
