@@ -366,6 +366,41 @@ def run_serving_suite(n_requests, seed=7, load=0.8, compare_requests=300):
     return out
 
 
+def precision_check(G, device, serving_sample=8, max_steps=1.5e9):
+    """The error of the mixed-precision path against the plain FP64 path
+    (the same kernels in FP64, the same random numbers), stated with the
+    results: the d = 10 workload at the paper's penalty weight omega = 1
+    (where the iteration converges) for 2 iterations, and a sample of the
+    serving mix's requests (the first ones with at most max_steps
+    path-steps, European and American alike; a request's served result
+    equals its stand-alone solve bit for bit).  Relative errors of the price
+    and of the largest delta."""
+    import numpy as np
+
+    def pair(cfg):
+        out = []
+        for prec in ("mixed", "fp64"):
+            s = G.Solver(cfg, precision=prec, device=device)
+            r = s.solve(use_graph=0)
+            s.close()
+            out.append((r.price, np.array(r.delta[:cfg["d"]]), r.status))
+        (pm, dm, sm), (pf, df, sf) = out
+        return {"price_rel_err": abs(pm - pf) / max(abs(pf), 1e-300),
+                "delta_rel_err": float(np.max(np.abs(dm - df)) / max(np.max(np.abs(df)), 1e-300)),
+                "status": [sm, sf]}
+
+    res = {"tolerance": 1e-4}
+    res["d10_omega1_K_it2"] = pair(workloads.config(CONFIG, K_it=2, **{"lambda": 1.0}))
+    sample = [r for r in workloads.serving_mix(2000, seed=7) if workloads.path_steps(r) <= max_steps]
+    sample = sample[:serving_sample]
+    rows = [dict(pair(r), d=r["d"], eta=r["eta"], **{"lambda": r["lambda"]}) for r in sample]
+    res["serving_sample"] = {"requests": len(rows),
+                             "max_price_rel_err": max(x["price_rel_err"] for x in rows),
+                             "max_delta_rel_err": max(x["delta_rel_err"] for x in rows),
+                             "per_request": rows}
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -470,6 +505,7 @@ def run_ours(args):
     chk = G.Solver(workloads.config(CONFIG, **{"lambda": 1.0}), precision="mixed", device=local)
     r1 = chk.solve(use_graph=1)
     chk.close()
+    precision = None if args.no_fp64 else precision_check(G, local)
     omega1 = {"lambda": 1.0, "price": r1.price, "delta": list(r1.delta[:10]),
               "resid_l2": list(r1.resid_l2[:cfg["K_it"]]), "status": r1.status}
     # the other configured workloads (whole solves, graph replay, device time)
@@ -569,6 +605,7 @@ def run_ours(args):
                           "iteration contracts (error bound (lambda T)^k / k!): the iterates of this "
                           "throughput workload grow over its 12 iterations; see solve_omega1"},
         "solve_omega1": omega1,
+        "precision_error": precision,
         "other_workloads": others,
         "paper_timing_context": paper,
         "cpu_baseline": cpu,

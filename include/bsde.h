@@ -159,7 +159,11 @@ BSDE_API int bsde_set_grid(bsde_ctx* ctx, int n, const double* lo, const double*
 
 typedef struct {
   int M;            /* Monte Carlo paths per point                        */
-  int N_steps;      /* Euler steps per path, on [t_i, T]                  */
+  int N_steps;      /* Euler steps per path, on [t_i, T]; the path kernel
+                       keeps per-step volatility coefficients and Philox
+                       words in shared memory (about 12 d bytes per step
+                       with FP32 paths, 20 d with FP64), so very long
+                       paths give BSDE_ERR_INVALID_ARG                  */
   int eta;          /* maximal total degree of the basis                  */
   double q;         /* hyperbolic index of eq. hyper_set (1 = total degree) */
   int K_it;         /* Picard iterations, 1..BSDE_MAX_IT                  */
