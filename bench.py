@@ -249,12 +249,12 @@ def arrival_times(n, rate_hz, seed):
     return out
 
 
-def run_serving(reqs, arrivals, precision="mixed", slots=16, policy="fifo"):
+def run_serving(reqs, arrivals, precision="mixed", slots=16, policy="fifo", large_slots=2):
     """Continuous-batching serving: the requests of the mix submitted to
     bsde_server at their arrival times (seconds from the start).  Returns
     p50/p99 latency (submit to completion) and throughput."""
     import paper_1102_4666_gb300 as G
-    srv = G.Server(max_slots=slots, precision=precision, policy=policy)
+    srv = G.Server(max_slots=slots, precision=precision, policy=policy, large_slots=large_slots)
     t_start = time.perf_counter()
     ids = []
     for r, t_arr in zip(reqs, arrivals):
@@ -272,6 +272,7 @@ def run_serving(reqs, arrivals, precision="mixed", slots=16, policy="fifo"):
             bad += 1
     srv.close()
     return {"requests": len(reqs), "precision": precision, "slots": slots, "policy": policy,
+            "large_slots": large_slots if policy == "size_lanes" else None,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "path_steps_per_s": st["path_steps"] / wall, "busy_path_steps_per_s": st["path_steps_per_s"],
             "wall_s": wall, "failed": bad}

@@ -418,8 +418,8 @@ typedef struct bsde_server bsde_server;
                                   less work than the average so far is
                                   admitted at once (high-priority stream);
                                   one with at least the average work waits
-                                  while another of its lane runs, and the
-                                  smaller requests behind it pass it      */
+                                  while large_slots others of its lane run,
+                                  and the smaller requests behind it pass it */
 
 typedef struct {
   int device;
@@ -427,6 +427,8 @@ typedef struct {
   size_t mem_budget;    /* device bytes for resident requests            */
   int precision;        /* BSDE_PREC_*                                   */
   int policy;           /* BSDE_POLICY_*                                 */
+  int large_slots;      /* BSDE_POLICY_SIZE_LANES: requests of the large
+                           lane resident at once (0: 2)                  */
 } bsde_server_opts;
 
 typedef struct {

@@ -108,7 +108,7 @@ class bsde_peer_exchange(ctypes.Structure):
 
 class bsde_server_opts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_slots", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
-                ("precision", ctypes.c_int), ("policy", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("policy", ctypes.c_int), ("large_slots", ctypes.c_int)]
 
 
 class bsde_request(ctypes.Structure):
@@ -552,12 +552,14 @@ class Server:
     (0: no limit) in the order of the policy: "fifo", "shortest" (fewest
     path-steps K_it n M N first), "response_ratio" (highest
     (wait + service) / service first) or "size_lanes" (arrival order; a
-    request with at least the average work waits while another such runs,
-    smaller ones pass it)."""
+    request with at least the average work waits while large_slots such
+    requests run, smaller ones pass it)."""
 
-    def __init__(self, device=0, max_slots=16, mem_budget=0, precision="mixed", policy="fifo"):
+    def __init__(self, device=0, max_slots=16, mem_budget=0, precision="mixed", policy="fifo",
+                 large_slots=2):
         o = bsde_server_opts()
         o.device, o.max_slots, o.mem_budget = device, max_slots, mem_budget
+        o.large_slots = large_slots
         o.policy = {"fifo": POLICY_FIFO, "shortest": POLICY_SHORTEST,
                     "response_ratio": POLICY_RESPONSE_RATIO, "size_lanes": POLICY_SIZE_LANES}[policy]
         o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64

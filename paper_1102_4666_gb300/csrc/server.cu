@@ -88,13 +88,13 @@ bool bsde_server::admit_one(std::unique_lock<std::mutex>& lk) {
       if (queue[q]->work < queue[pick]->work) pick = q;
   } else if (opts.policy == BSDE_POLICY_SIZE_LANES) {
     // arrival order, but a request with at least the average work waits
-    // while another such request runs; smaller ones pass it
+    // while large_slots such requests run; smaller ones pass it
     const double sum = work_sum, cnt = (double)work_count;
     bool found = false;
     for (size_t q = 0; q < queue.size(); ++q) {
       const double w = queue[q]->work;
       const bool large = w >= (sum + w) / (cnt + 1.0);
-      if (!large || large_running == 0) {
+      if (!large || large_running < (opts.large_slots > 0 ? opts.large_slots : 2)) {
         pick = q;
         found = true;
         break;
@@ -221,7 +221,8 @@ void bsde_server::loop() {
 extern "C" {
 
 int bsde_server_create(bsde_server** out, const bsde_server_opts* o) {
-  if (!out || !o || o->max_slots < 1 || o->max_slots > 64 ||
+  if (!out || !o || o->max_slots < 1 || o->max_slots > 64 || o->large_slots < 0 ||
+      o->large_slots > 64 ||
       (o->precision != BSDE_PREC_FP64 && o->precision != BSDE_PREC_MIXED) ||
       (o->policy != BSDE_POLICY_FIFO && o->policy != BSDE_POLICY_SHORTEST &&
        o->policy != BSDE_POLICY_RESPONSE_RATIO && o->policy != BSDE_POLICY_SIZE_LANES))

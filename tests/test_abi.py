@@ -51,7 +51,7 @@ int main(void) {
   P(bsde_penalty) O(bsde_penalty, obstacle)
   P(bsde_solve_params) O(bsde_solve_params, seed) O(bsde_solve_params, allow_underdetermined) O(bsde_solve_params, eval_mode) O(bsde_solve_params, paths_ppt) O(bsde_solve_params, ls_mode) O(bsde_solve_params, gram_splits)
   P(bsde_report) O(bsde_report, ms_total) O(bsde_report, kernel_launches) O(bsde_report, resid_linf) O(bsde_report, rank)
-  P(bsde_server_opts) O(bsde_server_opts, precision) O(bsde_server_opts, policy)
+  P(bsde_server_opts) O(bsde_server_opts, precision) O(bsde_server_opts, policy) O(bsde_server_opts, large_slots)
   P(bsde_request) O(bsde_request, params) O(bsde_request, hi) O(bsde_request, n)
   P(bsde_server_stats) O(bsde_server_stats, path_steps_per_s)
   P(bsde_peer_exchange) O(bsde_peer_exchange, flag) O(bsde_peer_exchange, c_len) O(bsde_peer_exchange, wait_ms) O(bsde_peer_exchange, pushed) O(bsde_peer_exchange, user)

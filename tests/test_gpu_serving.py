@@ -63,7 +63,7 @@ def test_admission_by_memory_budget():
     srv.close()
 
 
-def _completion_order(policy, slots=1):
+def _completion_order(policy, slots=1, large_slots=2):
     """Submit two long requests and then a short one to a server with `slots`
     slots and return the order in which they complete (0, 1: long; 2: short)."""
     import time
@@ -71,7 +71,7 @@ def _completion_order(policy, slots=1):
     import paper_1102_4666_gb300 as G
     long_req = workloads.config("c3", K_it=2)  # 1e9 path-steps
     short_req = workloads.config("c3", n=500, M=1000, K_it=1)
-    srv = G.Server(max_slots=slots, precision="mixed", policy=policy)
+    srv = G.Server(max_slots=slots, precision="mixed", policy=policy, large_slots=large_slots)
     ids = [srv.submit(long_req), srv.submit(long_req, seed=99), srv.submit(short_req)]
     done = []
     t0 = time.monotonic()
@@ -108,8 +108,9 @@ def test_response_ratio_policy_serves_short_first_and_everyone():
 
 
 def test_size_lanes_policy_runs_large_requests_one_at_a_time():
-    """Two slots: the second long request (at least the average work) waits
-    while the first runs, and the short one behind it passes it."""
-    order = _completion_order("size_lanes", slots=2)
+    """Two slots and one large-lane slot: the second long request (at least
+    the average work) waits while the first runs, and the short one behind
+    it passes it."""
+    order = _completion_order("size_lanes", slots=2, large_slots=1)
     assert sorted(order) == [0, 1, 2]
     assert order.index(2) < order.index(1) and order.index(0) < order.index(1)
