@@ -501,6 +501,16 @@ def test_errors_are_status_codes(G):
     s3 = solver(G, bad, "fp64")
     assert s3.solve(check=False).status == G.ERR_INVALID_ARG
     s3.close()
+    # paths too long for the path kernel's shared-memory tables (per-step
+    # volatility coefficients and Philox words): refused before any launch,
+    # and the context stays usable
+    long_n = workloads.config("c4", n=200, M=64, N=20000, eta=2, K_it=1)
+    s7 = solver(G, long_n, "mixed")
+    assert s7.solve(check=False).status == G.ERR_INVALID_ARG
+    assert "shared-memory" in G.lib().bsde_last_error(s7.h).decode()
+    s7.cfg = workloads.config("c4", n=200, M=64, N=400, eta=2, K_it=1)
+    assert s7.solve(check=False).status == G.OK
+    s7.close()
     # empty inputs: no paths, no steps, K_it beyond the report
     s6 = solver(G, workloads.config("c1", n=100, M=10, N=3, eta=2, K_it=1), "mixed")
     for kw in (dict(M=0), dict(N_steps=0), dict(K_it=65)):
