@@ -208,9 +208,8 @@ __device__ __forceinline__ R sigma_j(const Args<R, D>& a, const R* tabs, int j, 
     const R r = tanh_r<VK == VK_TANH_ABS>(a, j, xj);
     R A, B;
     if constexpr (sizeof(R) == 4) {
-      const float2 ab = reinterpret_cast<const float2*>(tabs)[j];  // one 64-bit load
-      A = ab.x;
-      B = ab.y;
+      A = tabs[4 * (j >> 1) + (j & 1)];
+      B = tabs[4 * (j >> 1) + 2 + (j & 1)];
     } else {
       A = tabs[2 * j];
       B = tabs[2 * j + 1];
@@ -568,6 +567,22 @@ __device__ __forceinline__ void eval_tree(const Args<R, D>& a, const R* __restri
   gen = r.b + R(0.5) * ((R(1) - a.rho) * r.dg + a.rho * r.ss);
 }
 
+// correlated increment y = sqrt(h) (L Z)_j of asset j (prefix sum `pre` of
+// the constant-correlation factor, or the triangular product)
+template <bool CC, int G, typename R, int D>
+__device__ __forceinline__ R corr_inc(const Args<R, D>& a, const R (&z)[G * D], int gs, int j, R& pre) {
+  if constexpr (CC) {
+    const R y = a.Ld[j] * z[gs * D + j] + pre;
+    pre += a.Lc[j] * z[gs * D + j];
+    return y;
+  } else {
+    R y = 0;
+#pragma unroll
+    for (int q = 0; q <= j; ++q) y += a.L[j][q] * z[gs * D + q];
+    return y;
+  }
+}
+
 // One Euler step of every asset of X (in place), with the sqrt(h)-scaled
 // normals z[gs D .. gs D + D) of a group of G steps and the volatility row
 // tabs of the step: X_j += h (r - delta_j) + sigma_j (y_j - h sigma_j / 2),
@@ -578,29 +593,48 @@ template <int VK, bool CC, int G, typename R, int D>
 __device__ __forceinline__ void euler_step(const Args<R, D>& a, const R* tabs, const R (&z)[G * D],
                                            int gs, R nhh, R h, R (&X)[D]) {
   R pre = 0;  // running sum of the constant-correlation factor
-  float4 q4;  // (A_j, B_j, A_j+1, B_j+1) of the FP32 tanh families
+  if constexpr ((VK == VK_TANH || VK == VK_TANH_ABS) && sizeof(R) == 4) {
+    // FP32 tanh families: assets in pairs, the pair's table row
+    // (A_j, A_j+1, B_j, B_j+1) in one 128-bit load, and the pair's
+    // arithmetic in packed FP32x2 instructions (the same IEEE operations as
+    // the scalar form, half the instructions)
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    // correlated increment y = sqrt(h) (L Z)_j
-    R y;
-    if constexpr (CC) {
-      y = a.Ld[j] * z[gs * D + j] + pre;
-      pre += a.Lc[j] * z[gs * D + j];
-    } else {
-      y = 0;
+    for (int j = 0; j < D; j += 2) {
+      const float4 q4 = reinterpret_cast<const float4*>(tabs)[j >> 1];
+      const R y0 = corr_inc<CC, G>(a, z, gs, j, pre);
+      if (j + 1 < D) {
+        const R y1 = corr_inc<CC, G>(a, z, gs, j + 1, pre);
+        const float2 xx = make_float2(X[j], X[j + 1]);
+        float2 t = __ffma2_rn(xx, make_float2(2.8853900817779268f, 2.8853900817779268f),
+                              make_float2(a.kc[j], a.kc[j + 1]));  // 2 log2(e) (x - kappa)
+        if constexpr (VK == VK_TANH_ABS) t = make_float2(fabsf(t.x), fabsf(t.y));
+        float e0, e1, r0, r1;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e0) : "f"(t.x));
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(t.y));
+        const float2 ep = __fadd2_rn(make_float2(e0, e1), make_float2(1.0f, 1.0f));
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(ep.x));
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(ep.y));
+        const float2 sig = __ffma2_rn(make_float2(q4.z, q4.w), make_float2(r0, r1), make_float2(q4.x, q4.y));
+        // X + h rd_j + sigma (y - h sigma / 2)
+        const float2 in = __ffma2_rn(make_float2(nhh, nhh), sig, make_float2(y0, y1));
+        const float2 base = __ffma2_rn(make_float2(h, h), make_float2(a.rd[j], a.rd[j + 1]), xx);
+        const float2 xn = __ffma2_rn(sig, in, base);
+        X[j] = xn.x;
+        X[j + 1] = xn.y;
+      } else {
+        const R r = tanh_r<VK == VK_TANH_ABS>(a, j, X[j]);
+        const R sig = q4.x + q4.z * r;
+        X[j] = sig * (nhh * sig + y0) + (h * a.rd[j] + X[j]);
+      }
+    }
+  } else {
 #pragma unroll
-      for (int q = 0; q <= j; ++q) y += a.L[j][q] * z[gs * D + q];
+    for (int j = 0; j < D; ++j) {
+      const R y = corr_inc<CC, G>(a, z, gs, j, pre);
+      const R sig = sigma_j<VK>(a, tabs, j, X[j]);
+      // X + (r - delta_j - sigma^2/2) h + sigma y = X + h rd_j + sigma (y - h sigma / 2)
+      X[j] = sig * (nhh * sig + y) + (h * a.rd[j] + X[j]);
     }
-    R sig;
-    if constexpr ((VK == VK_TANH || VK == VK_TANH_ABS) && sizeof(R) == 4) {
-      if ((j & 1) == 0) q4 = reinterpret_cast<const float4*>(tabs)[j >> 1];
-      const R r = tanh_r<VK == VK_TANH_ABS>(a, j, X[j]);
-      sig = (j & 1) ? (q4.z + q4.w * r) : (q4.x + q4.y * r);
-    } else {
-      sig = sigma_j<VK>(a, tabs, j, X[j]);
-    }
-    // X + (r - delta_j - sigma^2/2) h + sigma y = X + h rd_j + sigma (y - h sigma / 2)
-    X[j] = sig * (nhh * sig + y) + (h * a.rd[j] + X[j]);
   }
 }
 
@@ -654,9 +688,13 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     const R ts = ti + (R)s * h;
     R v = 0;
     if constexpr (VK == VK_TANH || VK == VK_TANH_ABS) {
-      const int j = c >> 1;
+      // FP32 rows: (A_j, A_j+1, B_j, B_j+1) per pair of assets, so that one
+      // 128-bit load gives the pair's A and B as two float2; FP64 rows:
+      // (A_j, B_j) per asset
+      const int j = sizeof(R) == 4 ? 2 * (c >> 2) + (c & 1) : c >> 1;
+      const bool isB = sizeof(R) == 4 ? ((c >> 1) & 1) != 0 : (c & 1) != 0;
       const R phi = a.vol_sin ? a.vb * Math<R>::sin((R)(j + 1) + ts) : a.vb * Math<R>::exp_acc(-ts);
-      v = (c & 1) ? R(-2) * phi : a.va[j < D ? j : 0] + phi;
+      v = isB ? R(-2) * phi : a.va[j < D ? j : 0] + phi;
     } else if constexpr (VK == VK_DUPIRE) {
       const R ew = Math<R>::exp_acc(R(-0.05) * Math<R>::sqrt(ts));
       v = (c == 0) ? R(0.72) * ew
