@@ -72,24 +72,27 @@ struct Math<float> {
   }
   __device__ __forceinline__ static void box_muller(uint32_t w0, uint32_t w1, float& z0,
                                                     float& z1, float k) {
-    const float u0 = fmaf(__uint2float_rn(w0), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    // u0 = (w0 + 1/2) 2^-32 and the angle 2 pi u1 - pi in (-pi, pi] (straight
+    // from w1; cos/sin flip sign) in one packed FP32x2 multiply-add
+    const float2 ua = __ffma2_rn(make_float2(__uint2float_rn(w0), __uint2float_rn(w1)),
+                                 make_float2(2.3283064365386963e-10f, 1.4629180792671596e-09f),
+                                 make_float2(1.1641532182693481e-10f, -3.1415926528f));
     float lg;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(u0));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"(ua.x));
     // radius: r2 = lg * k >= 0 (lg <= 0, k < 0), one approximate square
     // root (sqrt(0) = 0 at u0 = 1: no clamp needed)
     const float r2 = lg * k;
     float rad, s, c;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(rad) : "f"(r2));
-    // angle 2 pi u1 - pi in (-pi, pi], straight from w1; cos/sin flip sign.
     // The .ftz forms: no operand here is subnormal (u0 >= 2^-33; r2 is 0 or
     // above 1e-20 for any step h >= 1e-10; |angle| is 0 or above 1e-9), so
     // flushing changes no result and saves the subnormal handling of the
     // non-ftz forms.
-    const float ang = fmaf(__uint2float_rn(w1), 1.4629180792671596e-09f, -3.1415926528f);
-    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(ang));
-    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(ang));
-    z0 = -rad * c;
-    z1 = -rad * s;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(ua.y));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(ua.y));
+    const float2 zz = __fmul2_rn(make_float2(-rad, -rad), make_float2(c, s));
+    z0 = zz.x;
+    z1 = zz.y;
   }
   // e^x = 2^(x log2 e); results below the normal range flush to 0
   __device__ __forceinline__ static float exp(float x) {

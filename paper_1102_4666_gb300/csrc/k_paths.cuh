@@ -627,6 +627,25 @@ __device__ __forceinline__ void euler_step(const Args<R, D>& a, const R* tabs, c
         X[j] = sig * (nhh * sig + y0) + (h * a.rd[j] + X[j]);
       }
     }
+  } else if constexpr (VK == VK_CONST && sizeof(R) == 4) {
+    // constant volatilities: the update of a pair of assets in packed FP32x2
+#pragma unroll
+    for (int j = 0; j < D; j += 2) {
+      const R y0 = corr_inc<CC, G>(a, z, gs, j, pre);
+      if (j + 1 < D) {
+        const R y1 = corr_inc<CC, G>(a, z, gs, j + 1, pre);
+        const float2 xx = make_float2(X[j], X[j + 1]);
+        const float2 sig = make_float2(a.va[j], a.va[j + 1]);
+        const float2 in = __ffma2_rn(make_float2(nhh, nhh), sig, make_float2(y0, y1));
+        const float2 base = __ffma2_rn(make_float2(h, h), make_float2(a.rd[j], a.rd[j + 1]), xx);
+        const float2 xn = __ffma2_rn(sig, in, base);
+        X[j] = xn.x;
+        X[j + 1] = xn.y;
+      } else {
+        const R sig = a.va[j];
+        X[j] = sig * (nhh * sig + y0) + (h * a.rd[j] + X[j]);
+      }
+    }
   } else {
 #pragma unroll
     for (int j = 0; j < D; ++j) {
