@@ -34,13 +34,14 @@ CONFIG = "c4"
 FP32_LANES = 128  # FP32 lanes per SM (sm_103a)
 # DRAM bytes (read + write) of one path-kernel launch per point, from an ncu
 # capture of the same kernel on the d = 10 workload with n = 800 points
-# (155.1 KB read, 0 B written: the partial sums stay in L2), scaled to a
+# (146.2 KB read, 0 B written: the partial sums stay in L2), scaled to a
 # launch over n points (the kernel reads the points and coefficients and
 # writes one partial sum per (point, chunk), both proportional to n).
-PATH_TRAFFIC_BYTES_PER_POINT = (155136.0 + 0.0) / 800.0
+PATH_TRAFFIC_BYTES_PER_POINT = (146176.0 + 0.0) / 800.0
 # instruction issue of the same capture: instructions per path-step and
 # instructions issued per SM cycle (of 4), and the MUFU (XU) pipe's share
-PATH_ISSUE = {"instructions_per_path_step": 305.2, "ipc": 2.67, "ipc_peak": 4.0, "xu_pipe_busy": 0.628}
+PATH_ISSUE = {"instructions_per_path_step": 292.9, "ipc": 2.64, "ipc_peak": 4.0, "xu_pipe_busy": 0.632,
+              "fma_heavy_pipe_busy": 0.601}
 
 
 def env_rank():
