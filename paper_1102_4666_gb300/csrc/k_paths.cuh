@@ -567,6 +567,89 @@ __device__ __forceinline__ void eval_tree(const Args<R, D>& a, const R* __restri
   gen = r.b + R(0.5) * ((R(1) - a.rho) * r.dg + a.rho * r.ss);
 }
 
+// The tree recursion with FP32 paths, the leaves folded in packed FP32x2: a
+// leaf carries only its coefficient c (every derivative of its Q is zero), so
+// its parent adds (z_x, zT_x) c to (Q, T) and (bt_x, st_x) c to (B, S) in two
+// __ffma2_rn, the coefficients stored twice in shared memory so that one
+// 64-bit load gives (c, c).  The interior folds are those of tree_children.
+// The same IEEE operations as tree_node up to additions of exact zeros (the
+// leaves' zero derivatives, st_0 = 0), so the same results.
+struct TreeAcc2 {
+  float2 vt;  // (Q, T): value at (tau, X_tau) and at (T, X_T)
+  float2 bs;  // (B, S): derivatives along bt and st
+  float ss, dg, sd;
+};
+
+template <int DP, int ETA, int DEPTH, int W, int IDX>
+__device__ __forceinline__ void tree_node2(const float2* __restrict__ beta2, const float2 (&PVT)[DP],
+                                           const float2 (&PBS)[DP], const float (&s2x2)[DP],
+                                           TreeAcc2& a);
+
+template <int DP, int ETA, int DEPTH, int W, int X, int IDX>
+__device__ __forceinline__ void tree_children2(const float2* __restrict__ beta2, const float2 (&PVT)[DP],
+                                               const float2 (&PBS)[DP], const float (&s2x2)[DP],
+                                               TreeAcc2& a) {
+  if constexpr (X < DP) {
+    if constexpr (DEPTH + 1 == ETA) {
+      const float2 cc = beta2[IDX];
+      a.vt = __ffma2_rn(PVT[X], cc, a.vt);
+      a.bs = __ffma2_rn(PBS[X], cc, a.bs);
+      if constexpr (DEPTH > 0 && X == W) a.sd = cc.x;
+    } else {
+      TreeAcc2 c;
+      tree_node2<DP, ETA, DEPTH + 1, X, IDX>(beta2, PVT, PBS, s2x2, c);
+      const float zx = PVT[X].x, zTx = PVT[X].y, btx = PBS[X].x, stx = PBS[X].y;
+      a.vt.x += zx * c.vt.x;
+      a.bs.x += zx * c.bs.x + btx * c.vt.x;
+      if constexpr (X > 0) {
+        a.bs.y += zx * c.bs.y + stx * c.vt.x;
+        a.ss += zx * c.ss + 2.f * stx * c.bs.y;
+        a.dg += zx * c.dg + s2x2[X] * c.sd;
+      } else {  // the time variate has no diffusion
+        a.bs.y += zx * c.bs.y;
+        a.ss += zx * c.ss;
+        a.dg += zx * c.dg;
+      }
+      if constexpr (DEPTH > 0 && X == W) a.sd = c.vt.x + zx * c.sd;
+      a.vt.y += zTx * c.vt.y;
+    }
+    tree_children2<DP, ETA, DEPTH, W, X + 1, IDX + tree_size(DP - X, ETA - DEPTH - 1)>(beta2, PVT, PBS,
+                                                                                      s2x2, a);
+  }
+}
+
+template <int DP, int ETA, int DEPTH, int W, int IDX>
+__device__ __forceinline__ void tree_node2(const float2* __restrict__ beta2, const float2 (&PVT)[DP],
+                                           const float2 (&PBS)[DP], const float (&s2x2)[DP],
+                                           TreeAcc2& a) {
+  const float c0 = beta2[IDX].x;
+  a.vt = make_float2(c0, c0);
+  a.bs = make_float2(0.f, 0.f);
+  a.ss = a.dg = a.sd = 0.f;
+  if constexpr (DEPTH < ETA) {
+    tree_children2<DP, ETA, DEPTH, W, (DEPTH == 0 ? 0 : W), IDX + 1>(beta2, PVT, PBS, s2x2, a);
+    // keep the coefficient loads of one group of leaves together
+    if constexpr (DEPTH == ETA - 1) asm volatile("" ::: "memory");
+  }
+}
+
+// PVT[v] = (z_v, zT_v), PBS[v] = (bt_v, st_v): the reduced coordinates of
+// both evaluation points and the drift and diffusion directions
+template <int D, int ETA>
+__device__ __forceinline__ void eval_tree_x2(const Args<float, D>& a, const float2* __restrict__ beta2,
+                                             const float2 (&PVT)[D + 1], const float2 (&PBS)[D + 1],
+                                             float& u, float& gen, float& uT) {
+  constexpr int DP = D + 1;
+  float s2x2[DP];
+#pragma unroll
+  for (int v = 0; v < DP; ++v) s2x2[v] = 2.f * PBS[v].y * PBS[v].y;
+  TreeAcc2 r;
+  tree_node2<DP, ETA, 0, 0, 0>(beta2, PVT, PBS, s2x2, r);
+  u = r.vt.x;
+  uT = r.vt.y;
+  gen = r.bs.x + 0.5f * ((1.f - a.rho) * r.dg + a.rho * r.ss);
+}
+
 // correlated increment y = sqrt(h) (L Z)_j of asset j (prefix sum `pre` of
 // the constant-correlation factor, or the triangular product)
 template <bool CC, int G, typename R, int D>
@@ -670,10 +753,24 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
 
   // shared memory carve-up (dense evaluation: no multi-index or Chebyshev
   // tables; alpha holds the monomial coefficients, p of them)
+  // the prefix-tree evaluation (FP32 paths) keeps every coefficient twice
+  // (eval_tree_x2)
+  constexpr bool PAIRS = EV >= EV_TREE4 && sizeof(R) == 4;
   R* tab = reinterpret_cast<R*>(smem_raw);                         // N x tab_stride
-  R* s_alpha = tab + (size_t)a.N * a.tab_stride;                   // p
-  R* s_cp = s_alpha + a.p;                                          // DP x DP
-  size_t off = ((size_t)a.N * a.tab_stride + a.p + DP * DP) * sizeof(R);
+  R* s_alpha;                                                       // p (2 p with PAIRS)
+  R* s_cp;                                                          // DP x DP
+  size_t off;
+  if constexpr (PAIRS) {
+    // 16-byte aligned for the float2 loads of the coefficient pairs
+    const size_t aoff = ((size_t)a.N * a.tab_stride * sizeof(R) + 15) & ~(size_t)15;
+    s_alpha = reinterpret_cast<R*>(smem_raw + aoff);
+    s_cp = s_alpha + 2 * a.p;
+    off = aoff + ((size_t)2 * a.p + DP * DP) * sizeof(R);
+  } else {
+    s_alpha = tab + (size_t)a.N * a.tab_stride;
+    s_cp = s_alpha + a.p;
+    off = ((size_t)a.N * a.tab_stride + a.p + DP * DP) * sizeof(R);
+  }
   off = (off + 15) & ~(size_t)15;
   uint2* s_pairs = reinterpret_cast<uint2*>(smem_raw + off);
   uint8_t* s_nnz = smem_raw + off;
@@ -722,7 +819,12 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     tab[idx] = v;
   }
   for (int l = tid; l < a.p; l += tpb) {
-    s_alpha[l] = a.alpha[l];
+    if constexpr (PAIRS) {
+      s_alpha[2 * l] = a.alpha[l];
+      s_alpha[2 * l + 1] = a.alpha[l];
+    } else {
+      s_alpha[l] = a.alpha[l];
+    }
     if constexpr (EV == EV_TABLES) {
       s_pairs[l] = a.pairs[l];
       s_nnz[l] = a.nnz[l];
@@ -887,7 +989,17 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     if constexpr (SYNC_EVAL) __syncthreads();
 
     R u = 0, gsum = 0, uT = 0;
-    if constexpr (EV != EV_TABLES) {
+    if constexpr (PAIRS) {
+      float2 PVT[DP], PBS[DP];
+      PVT[0] = make_float2((tau - a.ctr[0]) * a.sc[0], (a.T - a.ctr[0]) * a.sc[0]);
+      PBS[0] = make_float2(a.sc[0], 0.f);
+#pragma unroll
+      for (int v = 1; v < DP; ++v) {
+        PVT[v] = make_float2((Xtau[v - 1] - a.ctr[v]) * a.sc[v], (X[v - 1] - a.ctr[v]) * a.sc[v]);
+        PBS[v] = make_float2(drift_s[v - 1] * a.sc[v], sig_s[v - 1] * a.sc[v]);
+      }
+      eval_tree_x2<D, EV>(a, reinterpret_cast<const float2*>(s_alpha), PVT, PBS, u, gsum, uT);
+    } else if constexpr (EV != EV_TABLES) {
       R z[DP], zT[DP], bt[DP], st[DP];
       z[0] = (tau - a.ctr[0]) * a.sc[0];
       zT[0] = (a.T - a.ctr[0]) * a.sc[0];
@@ -973,9 +1085,13 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
 // dynamic shared memory of the path kernel; dense: p is the number of
 // monomial coefficients and there are no per-thread tables
 inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bool dense,
-                         int tab_stride) {
+                         int tab_stride, bool pairs) {
   const int dp = d + 1;
-  size_t off = ((size_t)N * tab_stride + p + dp * dp) * rsize;
+  // the volatility table, 16-byte aligned; the coefficients (twice when
+  // `pairs`: the prefix-tree evaluation with FP32 paths reads them in pairs)
+  size_t off = (size_t)N * tab_stride * rsize;
+  if (pairs) off = (off + 15) & ~(size_t)15;
+  off += ((size_t)p * (pairs ? 2 : 1) + dp * dp) * rsize;
   off = (off + 15) & ~(size_t)15;
   if (!dense) {
     off += (size_t)p * sizeof(uint2);
@@ -1107,7 +1223,8 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
     else
       a.alpha = reinterpret_cast<const R*>(P.beta);
   }
-  const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense, a.tab_stride);
+  const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense, a.tab_stride,
+                                dense && P.tree > 0 && sizeof(R) == 4);
   const int vk = (m.vol_kind == 0)   ? VK_CONST
                  : (m.vol_kind == 1) ? VK_TANH_ABS
                  : (m.vol_kind == 3) ? VK_DUPIRE

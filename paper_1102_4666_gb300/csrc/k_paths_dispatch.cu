@@ -14,9 +14,12 @@ DECL(1) DECL(2) DECL(3) DECL(4) DECL(5) DECL(6) DECL(7) DECL(8) DECL(9) DECL(10)
 int paths_supported_d(int d) { return d >= 1 && d <= 10; }
 
 size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed, bool dense) {
-  // the tanh families tabulate two coefficients per asset and step
+  // an upper bound for every volatility family and evaluation form: the tanh
+  // families tabulate two coefficients per asset and step (rows padded to 16
+  // bytes), and a dense evaluation with FP32 paths may keep its coefficients
+  // twice (the prefix-tree form)
   return paths::smem_bytes(d, p, eta < 1 ? 1 : eta, N, tpb, mixed ? sizeof(float) : sizeof(double),
-                           dense, 2 * (d < 3 ? 3 : d));
+                           dense, (2 * (d < 3 ? 3 : d) + 3) & ~3, dense && mixed);
 }
 
 cudaError_t launch_paths(const ModelHost& m, const GridHost& g, const ProblemDev& P, int M, int N,
