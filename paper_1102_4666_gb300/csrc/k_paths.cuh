@@ -376,18 +376,23 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
 // from each monomial with a variate v repeated e >= 2 times, e (e - 1)
 // st_v^2 times the product of its other factors; the index patterns are
 // compile-time constants, so each coefficient gets only its own terms.
-template <typename R, int D>
+// CS = 2 (FP32 paths only): every coefficient is stored twice, and the four
+// accumulations of the innermost level, (ev, eT) += f (z_l, zT_l) and
+// (eb, es) += f (bt_l, st_l), run as two packed FP32x2 multiply-adds on an
+// (f, f) load -- the same IEEE operations (st_0 = 0 adds an exact zero).
+template <typename R, int D, int CS = 1>
 __device__ __forceinline__ void eval_dense4(const Args<R, D>& a, const R* __restrict__ beta,
                                             const R (&z)[D + 1], const R (&zT)[D + 1],
                                             const R (&bt)[D + 1], const R (&st)[D + 1], R& u,
                                             R& gen, R& uT) {
+  static_assert(CS == 1 || (CS == 2 && sizeof(R) == 4), "paired coefficients are FP32 only");
   constexpr int DP = D + 1;
   constexpr int NQ = DP * (DP + 1) / 2;
   constexpr int NC = DP * (DP + 1) * (DP + 2) / 6;
-  const R* bg = beta + 1;
-  const R* bq = bg + DP;
-  const R* bc3 = bq + NQ;
-  const R* bc4 = bc3 + NC;
+  const R* bg = beta + CS;
+  const R* bq = bg + CS * DP;
+  const R* bc3 = bq + CS * NQ;
+  const R* bc4 = bc3 + CS * NC;
   R s2[DP];  // st_v^2
 #pragma unroll
   for (int v = 0; v < DP; ++v) s2[v] = st[v] * st[v];
@@ -395,29 +400,37 @@ __device__ __forceinline__ void eval_dense4(const Args<R, D>& a, const R* __rest
   int iq = 0, ic = 0, i4 = 0;
 #pragma unroll
   for (int i = 0; i < DP; ++i) {
-    R bv = bg[i], bb = R(0), bs = R(0), bss = R(0), bT = bg[i];
+    R bv = bg[CS * i], bb = R(0), bs = R(0), bss = R(0), bT = bg[CS * i];
 #pragma unroll
     for (int j = 0; j < DP; ++j) {
       if (j < i) continue;
-      const R q = bq[iq++];
+      const R q = bq[CS * iq++];
       R av = q, ab = R(0), as = R(0), ass = R(0), aT = q;
       if (i == j && i > 0) diag += R(2) * s2[i] * q;
 #pragma unroll
       for (int k = 0; k < DP; ++k) {
         if (k < j) continue;
-        const R t = bc3[ic++];
+        const R t = bc3[CS * ic++];
         R ev = t, eb = R(0), es = R(0), eT = t;
+        float2 EVT = make_float2(t, t), EBS = make_float2(0.f, 0.f);  // CS = 2: (ev, eT), (eb, es)
         if (i == j && j < k && i > 0) diag += R(2) * s2[i] * t * z[k];
         if (i < j && j == k && j > 0) diag += R(2) * s2[j] * t * z[i];
         if (i == j && j == k && i > 0) diag += R(6) * s2[i] * t * z[i];
 #pragma unroll
         for (int l = 0; l < DP; ++l) {
           if (l < k) continue;
-          const R f = bc4[i4++];
-          ev += f * z[l];
-          eb += f * bt[l];
-          if (l > 0) es += f * st[l];
-          eT += f * zT[l];
+          const R f = bc4[CS * i4];
+          if constexpr (CS == 2) {
+            const float2 ff = reinterpret_cast<const float2*>(bc4)[i4];
+            EVT = __ffma2_rn(ff, make_float2(z[l], zT[l]), EVT);
+            EBS = __ffma2_rn(ff, make_float2(bt[l], st[l]), EBS);
+          } else {
+            ev += f * z[l];
+            eb += f * bt[l];
+            if (l > 0) es += f * st[l];
+            eT += f * zT[l];
+          }
+          ++i4;
           if (i == j && j == k && k == l) {
             if (i > 0) diag += R(12) * s2[i] * f * z[i] * z[i];
           } else if (i == j && j == k) {  // k < l
@@ -434,6 +447,12 @@ __device__ __forceinline__ void eval_dense4(const Args<R, D>& a, const R* __rest
           } else if (k == l) {  // i < j < k
             if (k > 0) diag += R(2) * s2[k] * f * z[i] * z[j];
           }
+        }
+        if constexpr (CS == 2) {
+          ev = EVT.x;
+          eT = EVT.y;
+          eb = EBS.x;
+          es = EBS.y;
         }
         // (z_k, bt_k, st_k, 0) * (ev, eb, es, 0)
         av += z[k] * ev;
@@ -753,9 +772,9 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
 
   // shared memory carve-up (dense evaluation: no multi-index or Chebyshev
   // tables; alpha holds the monomial coefficients, p of them)
-  // the prefix-tree evaluation (FP32 paths) keeps every coefficient twice
-  // (eval_tree_x2)
-  constexpr bool PAIRS = EV >= EV_TREE4 && sizeof(R) == 4;
+  // the prefix-tree and degree-4 evaluations (FP32 paths) keep every
+  // coefficient twice (eval_tree_x2, eval_dense4 with CS = 2)
+  constexpr bool PAIRS = (EV >= EV_TREE4 || EV == EV_DENSE4) && sizeof(R) == 4;
   R* tab = reinterpret_cast<R*>(smem_raw);                         // N x tab_stride
   R* s_alpha;                                                       // p (2 p with PAIRS)
   R* s_cp;                                                          // DP x DP
@@ -989,7 +1008,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
     if constexpr (SYNC_EVAL) __syncthreads();
 
     R u = 0, gsum = 0, uT = 0;
-    if constexpr (PAIRS) {
+    if constexpr (PAIRS && EV >= EV_TREE4) {
       float2 PVT[DP], PBS[DP];
       PVT[0] = make_float2((tau - a.ctr[0]) * a.sc[0], (a.T - a.ctr[0]) * a.sc[0]);
       PBS[0] = make_float2(a.sc[0], 0.f);
@@ -1015,7 +1034,7 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
       if constexpr (EV >= EV_TREE4)
         eval_tree<R, D, EV>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
       else if constexpr (EV == EV_DENSE4)
-        eval_dense4<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
+        eval_dense4<R, D, PAIRS ? 2 : 1>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
       else
         eval_dense3<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
     } else {
@@ -1224,7 +1243,7 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
       a.alpha = reinterpret_cast<const R*>(P.beta);
   }
   const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense, a.tab_stride,
-                                dense && P.tree > 0 && sizeof(R) == 4);
+                                dense && (P.tree > 0 || P.dense4) && sizeof(R) == 4);
   const int vk = (m.vol_kind == 0)   ? VK_CONST
                  : (m.vol_kind == 1) ? VK_TANH_ABS
                  : (m.vol_kind == 3) ? VK_DUPIRE
