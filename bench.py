@@ -37,10 +37,10 @@ FP32_LANES = 128  # FP32 lanes per SM (sm_103a)
 # (146.2 KB read, 0 B written: the partial sums stay in L2), scaled to a
 # launch over n points (the kernel reads the points and coefficients and
 # writes one partial sum per (point, chunk), both proportional to n).
-PATH_TRAFFIC_BYTES_PER_POINT = (146176.0 + 0.0) / 800.0
+PATH_TRAFFIC_BYTES_PER_POINT = (146944.0 + 0.0) / 800.0
 # instruction issue of the same capture: instructions per path-step and
 # instructions issued per SM cycle (of 4), and the MUFU (XU) pipe's share
-PATH_ISSUE = {"instructions_per_path_step": 292.9, "ipc": 2.64, "ipc_peak": 4.0, "xu_pipe_busy": 0.632,
+PATH_ISSUE = {"instructions_per_path_step": 294.3, "ipc": 2.67, "ipc_peak": 4.0, "xu_pipe_busy": 0.639,
               "fma_heavy_pipe_busy": 0.601}
 
 
@@ -571,7 +571,7 @@ def run_ours(args):
                                   ("one independent problem per rank" if world > 1 else "one GPU"),
                    "paths_launch_shape": list(shape) if shape else None,
                    "gram_splits": autotune.lookup_gram_splits(cfg, "mixed") or "default (one wave)"},
-        "roofline": {"bound": "alu", "kernel": "k_paths<VK_TANH,EV_DENSE3,CC,float,10>",
+        "roofline": {"bound": "alu", "kernel": "k_paths_lr<VK_TANH,EV_DENSE3,CC,float,10>",
                      "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": (PATH_TRAFFIC_BYTES_PER_POINT * cfg["n"]

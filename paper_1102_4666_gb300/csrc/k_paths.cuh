@@ -759,8 +759,9 @@ __device__ __forceinline__ void euler_step(const Args<R, D>& a, const R* tabs, c
   }
 }
 
+// One CTA's work: a point and a chunk of its paths (the kernels below).
 template <int VK, int EV, bool CC, typename R, int D>
-__global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R, D> a) {
+__device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int DP = D + 1;
   const int tid = threadIdx.x;
@@ -1101,6 +1102,29 @@ __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R
   }
 }
 
+
+// The path kernel.  FP32 paths with the dense degree-3 and degree-4
+// evaluations run with at most 96 registers per thread at d >= 8 (five
+// 128-thread CTAs per SM, a few values spilled outside the step loop) and 80
+// below (six); FP64 paths, the Chebyshev tables and the prefix-tree
+// evaluations (whose 256-thread CTAs share the instruction fetches of their
+// long straight-line evaluation) at two 256-thread CTAs with up to 128.
+// Measured per launch: d = 10 degree 3 17.41 -> 17.18 ms (80 registers:
+// 17.40), d = 5 degree 4 3.51 -> 3.41 ms, d = 6 degree 3 0.911 -> 0.896 ms
+// (96 registers: 0.914).
+template <int VK, int EV, bool CC, typename R, int D>
+__global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R, D> a) {
+  paths_cta<VK, EV, CC, R, D>(a);
+}
+template <int VK, int EV, bool CC, typename R, int D>
+__global__ void __maxnreg__(D >= 8 ? 96 : 80) k_paths_lr(const __grid_constant__ Args<R, D> a) {
+  paths_cta<VK, EV, CC, R, D>(a);
+}
+template <int EV, typename R>
+constexpr bool paths_lr() {
+  return sizeof(R) == 4 && (EV == EV_DENSE3 || EV == EV_DENSE4);
+}
+
 // dynamic shared memory of the path kernel; dense: p is the number of
 // monomial coefficients and there are no per-thread tables
 inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bool dense,
@@ -1127,13 +1151,22 @@ inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bo
   return off;
 }
 
+template <typename R, int D>
+cudaError_t launch_kernel(void (*kern)(Args<R, D>), const Args<R, D>& a, unsigned grid, int tpb,
+                          size_t smem, cudaStream_t st) {
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  kern<<<grid, tpb, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int VK, int EV, bool CC, typename R, int D>
 cudaError_t launch_one(const Args<R, D>& a, unsigned grid, int tpb, size_t smem, cudaStream_t st) {
-  cudaError_t err = cudaFuncSetAttribute(k_paths<VK, EV, CC, R, D>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  k_paths<VK, EV, CC, R, D><<<grid, tpb, smem, st>>>(a);
-  return cudaGetLastError();
+  // only the kernel that runs is instantiated
+  if constexpr (paths_lr<EV, R>())
+    return launch_kernel<R, D>(k_paths_lr<VK, EV, CC, R, D>, a, grid, tpb, smem, st);
+  else
+    return launch_kernel<R, D>(k_paths<VK, EV, CC, R, D>, a, grid, tpb, smem, st);
 }
 
 template <int EV, bool CC, typename R, int D>
