@@ -759,6 +759,54 @@ __device__ __forceinline__ void euler_step(const Args<R, D>& a, const R* tabs, c
   }
 }
 
+// The states before and after the step s* that contains the random time
+// tau (the Brownian bridge needs both) are kept one of three ways:
+// * in shared memory (copy_smem): a predicated 128-bit store per four assets
+//   before and after every step, no registers held for the copies;
+// * behind a warp vote (copy_vote), which skips the copies in the ~3/4 of
+//   the steps where no lane of the warp is at its s*; with FP32 paths the
+//   state is then copied once per group of G steps and the group's steps are
+//   taken again after the loop (its normals drawn again);
+// * as predicated register moves before and after every step.
+// The same function takes each step, so the results do not depend on which.
+// Measured per launch (FP32): the shared-memory copies against the register
+// moves d = 10 degree 3 17.18 -> 16.84 ms, d = 6 degree 3 0.896 -> 0.887 ms,
+// d = 10 degree 4 4.84 -> 4.77 ms; against the vote and second pass d = 5
+// degree 4 3.42 -> 3.31 ms, degree 5 3.38 -> 3.26 ms, degree 6 4.63 -> 4.54
+// ms, but d = 4 degree 4 2.08 -> 2.14 ms (G = 1: the second pass is one
+// step) and d = 3 degree 3 0.104 -> 0.106 ms; FP64 paths keep the registers
+// (and the vote).
+__host__ __device__ constexpr bool copy_vote(int ev, int d) {
+  return d >= 3 && ev != EV_DENSE3 && !(ev >= EV_TREE4 && d >= 6);
+}
+__host__ __device__ constexpr bool copy_smem(int ev, bool fp32, int d) {
+  return fp32 && ev != EV_TABLES && d >= 4 && !(copy_vote(ev, d) && d % 4 == 0);
+}
+
+// A thread's d-dimensional FP32 state as ceil(d / 4) float4 in a
+// [quad][thread] array of row length `stride` (zero padding past d).
+template <int D, typename R>
+__device__ __forceinline__ void store_state(float4* p, int stride, const R (&X)[D]) {
+#pragma unroll
+  for (int q = 0; q < (D + 3) / 4; ++q) {
+    const int j = 4 * q;
+    p[(size_t)q * stride] = make_float4(X[j], j + 1 < D ? X[j + 1] : 0.f, j + 2 < D ? X[j + 2] : 0.f,
+                                        j + 3 < D ? X[j + 3] : 0.f);
+  }
+}
+template <int D, typename R>
+__device__ __forceinline__ void load_state(const float4* p, int stride, R (&X)[D]) {
+#pragma unroll
+  for (int q = 0; q < (D + 3) / 4; ++q) {
+    const float4 v = p[(size_t)q * stride];
+    const int j = 4 * q;
+    X[j] = v.x;
+    if (j + 1 < D) X[j + 1] = v.y;
+    if (j + 2 < D) X[j + 2] = v.z;
+    if (j + 3 < D) X[j + 3] = v.w;
+  }
+}
+
 // One CTA's work: a point and a chunk of its paths (the kernels below).
 template <int VK, int EV, bool CC, typename R, int D>
 __device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
@@ -807,6 +855,12 @@ __device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
   double* red = reinterpret_cast<double*>(smem_raw + off);          // 32
   // rounds 1-3 of the normals' Philox blocks (philox_prep), per block index
   uint4* s_ph = reinterpret_cast<uint4*>(smem_raw + off + 32 * sizeof(double));
+  // the states before and after step s* (copy_smem): [copy][quad][thread]
+  // float4 after the Philox table
+  constexpr bool XCOPY = copy_smem(EV, sizeof(R) == 4, D);
+  constexpr int NQ = (D + 3) / 4;
+  float4* s_xc = reinterpret_cast<float4*>(s_ph + (a.N + (4 / gcd_c(D, 4)) - 1) / (4 / gcd_c(D, 4)) *
+                                                     ((4 / gcd_c(D, 4)) * D / 4));
 
   const R ti = (R)a.pt[i];
   R x0[D];
@@ -884,21 +938,10 @@ __device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
     const int sstar = (int)(wN >> 32);
     const R theta = uniform_frac<R>((uint32_t)wN);
 
-    // The step s* that contains tau needs the states before and after it.
-    // The vote below is over the lanes that reach a copy together; a lane
-    // whose copy is due always votes for itself, so it is never skipped.
-    // Without the vote a copy is D predicated moves; the vote and its branch
-    // pay off from d = 3 on, except next to the dense evaluations of d >= 6
-    // (the degree-3 loops at any d), whose registers leave no room for it.
-    constexpr bool VOTE = D >= 3 && EV != EV_DENSE3 && !(EV >= EV_TREE4 && D >= 6);
-    // Where the copies go behind a vote (FP32 paths), the state is copied
-    // once per group of G steps instead, at the start of the group that
-    // contains s*, and the group's steps are taken again after the loop (its
-    // normals drawn again from the same counters): measured 38.7 -> 37.7 ms
-    // per d = 5 degree-4 solve.  Elsewhere the copies before and after every
-    // step are cheaper than that second pass (d = 3 and 6 with N = 10: 2.30
-    // -> 2.46 and 11.10 -> 11.75 ms per solve; d = 10 with N = 100 even).
-    // Same results either way (the same function takes each step).
+    // the states before and after step s* (copy_vote, copy_smem); the vote
+    // is over the lanes that reach a copy together, and a lane whose copy is
+    // due always votes for itself, so it is never skipped
+    constexpr bool VOTE = copy_vote(EV, D) && !XCOPY;
     constexpr bool REBUILD = sizeof(R) == 4 && VOTE;
     const int g_hit = sstar - sstar % G;  // first step of the group that contains s*
     R X[D], Xg[D], Xs[D], Xn[D];
@@ -935,6 +978,11 @@ __device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
         if (s < a.N) {
           if constexpr (REBUILD) {
             euler_step<VK, CC, G>(a, tab + s * a.tab_stride, z, gs, nhh, h, X);
+          } else if constexpr (XCOPY) {
+            const bool hit = (s == sstar);
+            if (hit) store_state<D>(s_xc + tid, tpb, X);
+            euler_step<VK, CC, G>(a, tab + s * a.tab_stride, z, gs, nhh, h, X);
+            if (hit) store_state<D>(s_xc + (size_t)NQ * tpb + tid, tpb, X);
           } else {
             const bool hit = (s == sstar);
             const bool any_hit = VOTE ? __any_sync(__activemask(), hit) : true;
@@ -983,6 +1031,11 @@ __device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
         for (int j = 0; j < D; ++j)
           if (s == sstar) Xn[j] = Xg[j];
       }
+    }
+
+    if constexpr (XCOPY) {
+      load_state<D>(s_xc + tid, tpb, Xs);
+      load_state<D>(s_xc + (size_t)NQ * tpb + tid, tpb, Xn);
     }
 
     // X at tau: Brownian bridge inside step s*, coefficients frozen at t_{s*}
@@ -1131,7 +1184,7 @@ constexpr bool paths_lr() {
 // dynamic shared memory of the path kernel; dense: p is the number of
 // monomial coefficients and there are no per-thread tables
 inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bool dense,
-                         int tab_stride, bool pairs) {
+                         int tab_stride, bool pairs, bool xcopy) {
   const int dp = d + 1;
   // the volatility table, 16-byte aligned; the coefficients (twice when
   // `pairs`: the prefix-tree evaluation with FP32 paths reads them in pairs)
@@ -1151,6 +1204,9 @@ inline size_t smem_bytes(int d, int p, int eta, int N, int tpb, size_t rsize, bo
   const int gcd = (d % 4 == 0) ? 4 : (d % 2 == 0) ? 2 : 1;
   const int G = 4 / gcd, NB = G * d / 4;
   off += (size_t)((N + G - 1) / G) * NB * 16;
+  // `xcopy` (copy_smem): the states before and after step s*, one row of
+  // ceil(d / 4) float4 per thread and copy
+  if (xcopy) off += (size_t)2 * ((d + 3) / 4) * tpb * 16;
   return off;
 }
 
@@ -1279,7 +1335,9 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
       a.alpha = reinterpret_cast<const R*>(P.beta);
   }
   const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense, a.tab_stride,
-                                dense && (P.tree > 0 || P.dense4) && sizeof(R) == 4);
+                                dense && (P.tree > 0 || P.dense4) && sizeof(R) == 4,
+                                dense && copy_smem(P.tree > 0 ? EV_TREE4 : P.dense4 ? EV_DENSE4 : EV_DENSE3,
+                                                   sizeof(R) == 4, D));
   const int vk = (m.vol_kind == 0)   ? VK_CONST
                  : (m.vol_kind == 1) ? VK_TANH_ABS
                  : (m.vol_kind == 3) ? VK_DUPIRE
