@@ -50,10 +50,15 @@ __host__ __device__ constexpr int sym(int dp, int a, int b) { return a * dp - a 
 template <typename R, int D>
 struct Args {
   R T, r, lam, K, s_dupire;
-  R rd[D];          // r - delta_j
-  R w[D], va[D], kappa[D];
+  // the per-asset constants read in pairs by packed FP32x2 instructions
+  // start on 16-byte boundaries of the parameter bank
+  alignas(16) R rd[D];  // r - delta_j
+  R w[D];
+  alignas(16) R va[D];
+  R kappa[D];
   R L[D][D];        // lower Cholesky factor of the correlation
-  R Ld[D], Lc[D];   // constant correlation: diagonal of L and its constant column below it
+  alignas(16) R Ld[D];  // constant correlation: diagonal of L and its constant column below it
+  alignas(16) R Lc[D];
   R Cp[D + 1][D + 1];  // correlation padded with a zero time row/column
   R ctr[D + 1], sc[D + 1];  // xi_v = (y_v - ctr_v) sc_v
   int N, M, n, p, eta, chunks, tpb, ppt, tab_stride;
@@ -61,7 +66,7 @@ struct Args {
   int payoff, obstacle, vol_sin;
   R vb;
   R rho;  // constant correlation (dense evaluation)
-  R kc[D];  // -2 log2(e) kappa_j: e^{2 (x - kappa)} = 2^{x 2 log2(e) + kc}
+  alignas(16) R kc[D];  // -2 log2(e) kappa_j: e^{2 (x - kappa)} = 2^{x 2 log2(e) + kc}
   uint32_t k;
   uint32_t key0, key1;  // Philox key
   uint32_t rk0[10], rk1[10];  // its ten round keys (kernel-parameter constants)
@@ -703,9 +708,20 @@ __device__ __forceinline__ void euler_step(const Args<R, D>& a, const R* tabs, c
 #pragma unroll
     for (int j = 0; j < D; j += 2) {
       const float4 q4 = reinterpret_cast<const float4*>(tabs)[j >> 1];
-      const R y0 = corr_inc<CC, G>(a, z, gs, j, pre);
       if (j + 1 < D) {
-        const R y1 = corr_inc<CC, G>(a, z, gs, j + 1, pre);
+        float y0, y1;
+        if constexpr (CC) {
+          // (y_j, y_j+1) = (Ld_j, Ld_j+1) (z_j, z_j+1) + (pre, pre + Lc_j z_j)
+          const float p1 = fmaf(a.Lc[j], z[gs * D + j], pre);
+          const float2 yy = __ffma2_rn(make_float2(a.Ld[j], a.Ld[j + 1]),
+                                       make_float2(z[gs * D + j], z[gs * D + j + 1]), make_float2(pre, p1));
+          pre = fmaf(a.Lc[j + 1], z[gs * D + j + 1], p1);
+          y0 = yy.x;
+          y1 = yy.y;
+        } else {
+          y0 = corr_inc<CC, G>(a, z, gs, j, pre);
+          y1 = corr_inc<CC, G>(a, z, gs, j + 1, pre);
+        }
         const float2 xx = make_float2(X[j], X[j + 1]);
         float2 t = __ffma2_rn(xx, make_float2(2.8853900817779268f, 2.8853900817779268f),
                               make_float2(a.kc[j], a.kc[j + 1]));  // 2 log2(e) (x - kappa)
@@ -724,6 +740,7 @@ __device__ __forceinline__ void euler_step(const Args<R, D>& a, const R* tabs, c
         X[j] = xn.x;
         X[j + 1] = xn.y;
       } else {
+        const R y0 = corr_inc<CC, G>(a, z, gs, j, pre);
         const R r = tanh_r<VK == VK_TANH_ABS>(a, j, X[j]);
         const R sig = q4.x + q4.z * r;
         X[j] = sig * (nhh * sig + y0) + (h * a.rd[j] + X[j]);
