@@ -43,48 +43,59 @@ __device__ __forceinline__ float to_tf32(float v) {
 
 // B[l][i] = prod over the active variates v of T_{nu_lv}(xi_v(t_i, x_i)),
 // xi_v = (2 y_v - (lo_v + hi_v)) / (hi_v - lo_v), Chebyshev T_e by the
-// three-term recurrence.  Each thread first tabulates T_0..T_eta of its
-// point's dp reduced coordinates in shared memory ([v][e][thread], read back
-// only by the same thread), so that the FP64 division and recurrence run
-// once per (point, variate) instead of once per (point, basis function,
-// active variate); the products are then formed in the same order as the
-// definition.  With split != 0 also writes the 3xTF32 operands of the
-// tensor-core Gram: hi = tf32(fp32(B)), lo = tf32(fp32(B) - hi).
-__global__ void k_basis(int n, int n_pad, int p, int dp, int eta, const uint2* __restrict__ pairs,
-                        const uint8_t* __restrict__ nnz, const double* __restrict__ t,
-                        const double* __restrict__ x, const __grid_constant__ BoxArgs box,
-                        double* __restrict__ B, float* __restrict__ Bhi,
-                        float* __restrict__ Blo, int split) {
-  extern __shared__ double cheb[];
-  const int tid = threadIdx.x, tpb = blockDim.x;
-  const int i = blockIdx.x * tpb + tid;
-  if (i >= n) return;
+// three-term recurrence.  A CTA takes 32 consecutive points and a range of
+// basis functions: its threads first tabulate T_0..T_eta of the points' dp
+// reduced coordinates in shared memory ([v][e][point]), so that the FP64
+// division and recurrence run once per (point, variate) and CTA; then each
+// warp forms the basis functions l = warp, warp + warps, ... of the range,
+// one lane per point (a 256-byte row segment of B per store), the products
+// in the order of the definition.  With split != 0 also writes the 3xTF32
+// operands of the tensor-core Gram: hi = tf32(fp32(B)), lo = tf32(fp32(B) -
+// hi).  The basis functions are split over gridDim.y ranges only as far as
+// needed for two CTAs per SM.
+constexpr int BASIS_PTS = 32;  // points per CTA of k_basis, one per lane
+
+__global__ void k_basis(int n, int n_pad, int p, int l_per, int dp, int eta,
+                        const uint2* __restrict__ pairs, const uint8_t* __restrict__ nnz,
+                        const double* __restrict__ t, const double* __restrict__ x,
+                        const __grid_constant__ BoxArgs box, double* __restrict__ B,
+                        float* __restrict__ Bhi, float* __restrict__ Blo, int split) {
+  extern __shared__ double cheb[];  // [v][e][point]
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int i0 = blockIdx.x * BASIS_PTS;
   const int ne = eta + 1;
-  for (int v = 0; v < dp; ++v) {
+  for (int idx = tid; idx < dp * BASIS_PTS; idx += nth) {
+    const int v = idx / BASIS_PTS, q = idx - v * BASIS_PTS;
+    const int i = i0 + q;
+    if (i >= n) continue;
     const double y = (v == 0) ? t[i] : x[(size_t)(v - 1) * n + i];
     const double xi = __ddiv_rn(__dsub_rn(__dmul_rn(2.0, y), __dadd_rn(box.lo[v], box.hi[v])),
                                 __dsub_rn(box.hi[v], box.lo[v]));
-    double* tv = cheb + (size_t)v * ne * tpb + tid;
+    double* tv = cheb + (size_t)v * ne * BASIS_PTS + q;
     tv[0] = 1.0;
-    if (eta >= 1) tv[tpb] = xi;
+    if (eta >= 1) tv[BASIS_PTS] = xi;
     double tm1 = 1.0, tc = xi;
     for (int e = 2; e <= eta; ++e) {
       const double tn = __dsub_rn(__dmul_rn(__dmul_rn(2.0, xi), tc), tm1);
       tm1 = tc;
       tc = tn;
-      tv[(size_t)e * tpb] = tc;
+      tv[(size_t)e * BASIS_PTS] = tc;
     }
   }
-  const int l0 = blockIdx.y * 32;
-  const int l1 = min(p, l0 + 32);
-  for (int l = l0; l < l1; ++l) {
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+  const int i = i0 + lane;
+  if (i >= n) return;
+  const int l0 = blockIdx.y * l_per;
+  const int l1 = min(p, l0 + l_per);
+  for (int l = l0 + warp; l < l1; l += nw) {
     const uint2 pr = pairs[l];
     const int nz = nnz[l];
     double val = 1.0;
     for (int a = 0; a < nz; ++a) {
       const uint32_t byte = ((a < 4 ? pr.x >> (8 * a) : pr.y >> (8 * (a - 4)))) & 0xffu;
       const int v = (int)(byte >> 4), e = (int)(byte & 15u);
-      val = __dmul_rn(val, cheb[((size_t)v * ne + e) * tpb + tid]);
+      val = __dmul_rn(val, cheb[((size_t)v * ne + e) * BASIS_PTS + lane]);
     }
     B[(size_t)l * n_pad + i] = val;
     if (split) {
@@ -118,13 +129,17 @@ void launch_basis(const ModelHost& m, const GridHost& g, const ProblemDev& P, bo
     box.hi[v] = g.hi[v];
   }
   const int dp = m.d + 1, eta = P.eta < 1 ? 1 : P.eta;
-  // Chebyshev table of T_0..T_eta per variate and thread, within 48 KB
-  int tpb = 128;
-  while (tpb > 32 && (size_t)dp * (eta + 1) * tpb * sizeof(double) > 48 * 1024) tpb >>= 1;
-  const size_t smem = (size_t)dp * (eta + 1) * tpb * sizeof(double);
+  const int tpb = 128;
+  const size_t smem = (size_t)dp * (eta + 1) * BASIS_PTS * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_basis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((P.n + tpb - 1) / tpb, (P.p + 31) / 32);
-  k_basis<<<grid, tpb, smem, st>>>(P.n, P.n_pad, P.p, dp, eta, P.pairs, P.nnz, P.t, P.x, box, P.B,
-                                   P.Bhi, P.Blo, mixed ? 1 : 0);
+  const int gx = (P.n + BASIS_PTS - 1) / BASIS_PTS;
+  const int want = (2 * device_sm_count() + gx - 1) / gx;
+  int gy = (P.p + 31) / 32;
+  if (gy > want) gy = want;
+  if (gy < 1) gy = 1;
+  const int l_per = (P.p + gy - 1) / gy;
+  gy = (P.p + l_per - 1) / l_per;
+  k_basis<<<dim3(gx, gy), tpb, smem, st>>>(P.n, P.n_pad, P.p, l_per, dp, eta, P.pairs, P.nnz, P.t, P.x,
+                                            box, P.B, P.Bhi, P.Blo, mixed ? 1 : 0);
 }
