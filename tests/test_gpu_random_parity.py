@@ -1,0 +1,75 @@
+"""Teacher-forced parity on seeded random configurations.
+
+Besides the hand-picked cases of test_gpu_parity.py, one Picard iteration
+(Algorithm 2) from the same alpha^k is compared with the FP64 oracle on
+configurations drawn at random, with a fixed seed, over every axis the
+kernels specialise on or branch over: the dimension d = 1..10 (one kernel
+family per d, with its own grouping of Euler steps into Philox blocks), the
+total degree (dense degree-3 and degree-4 loops, the prefix-tree recursion
+of degrees 4 to 6, the per-thread Chebyshev tables), hyperbolic index sets
+(eq. hyper_set), every volatility family, put and call payoffs, the payoff
+and raw obstacles of the penalised driver (eq. bsde-penal-2), penalty
+weights from 0 (European) to 100, positive and negative constant
+correlations, dividends, maturities, strikes and rates, and ragged sizes
+(n just above 2 p, M and N from 1).  Tolerances are those of the fixed
+cases: 1e-9 of the integrand's scale in FP64, MIXED_C_TOL of it in mixed
+precision, and 1e-9 relative on the FP64 coefficients alpha^{k+1}.
+"""
+import random
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import bsde_oracle as O
+from test_gpu_parity import MIXED_C_TOL, NTH, _alpha, _scale, rel
+
+pytestmark = pytest.mark.gpu
+
+N_CASES = 48
+
+
+def _random_case(k):
+    rng = random.Random(7000 + k)
+    d = rng.randint(1, 10)
+    eta = rng.randint(1, 6 if d <= 5 else 4)
+    q = rng.choice([1.0, 1.0, 1.0, 0.75])
+    nu = O.multi_index_set(d + 1, eta, q)
+    p = len(nu)
+    kind = rng.choice(["const", "abs_tanh", "sin_tanh", "dupire"])
+    if kind == "const":
+        vol = {"kind": "const", "a": [rng.uniform(0.1, 0.4) for _ in range(d)]}
+    elif kind == "dupire":
+        vol = {"kind": "dupire", "s": 100.0}
+    else:
+        vol = {"kind": kind, "a": rng.uniform(0.12, 0.25), "b": rng.uniform(0.02, 0.1),
+               "kappa": float(np.log(rng.uniform(90.0, 110.0)))}
+    # a constant correlation keeps the matrix positive definite above -1/(d-1)
+    rho = 0.0 if d == 1 else rng.choice([0.0, 0.3, 0.6, -0.05])
+    cfg = workloads.make(d=d, T=rng.choice([0.5, 1.0, 2.0]), r=rng.uniform(0.0, 0.05),
+                         K=rng.uniform(80.0, 120.0), S0=100.0, vol=vol, rho=rho,
+                         lam=rng.choice([0.0, 1.0, 100.0]), n=2 * p + rng.randint(1, 40),
+                         M=rng.randint(1, 70), N=rng.randint(1, 9), eta=eta, K_it=1,
+                         seed=rng.randint(1, 10**6), payoff=rng.choice(["put", "call"]), q=q,
+                         div=[rng.uniform(0.0, 0.03) for _ in range(d)],
+                         obstacle=rng.choice(["payoff", "raw"]))
+    ev = rng.choice([0, 0, 1])  # automatic (dense where it applies) or the per-thread tables
+    return cfg, nu, ev
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("k", range(N_CASES))
+def test_random_configuration(k, prec):
+    import paper_1102_4666_gb300 as G
+    cfg, nu, ev = _random_case(k)
+    a0 = _alpha(cfg, nu, seed=11 + k)
+    it_k = k % 5
+    s = G.Solver(cfg, precision=prec)
+    t, x, c, a1 = s.iterate(it_k, a0, eval_mode=ev)
+    s.close()
+    it = O.iteration(cfg, nu, a0, it_k, nthreads=NTH)
+    sc = _scale(cfg, nu, a0, t, x)
+    tol = 1e-9 if prec == "fp64" else MIXED_C_TOL
+    assert np.max(np.abs(c - it["c"])) < tol * sc, (cfg["d"], cfg["eta"], cfg["vol"]["kind"], ev)
+    if prec == "fp64":
+        assert rel(a1, it["alpha"]) < 1e-9
