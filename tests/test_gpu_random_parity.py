@@ -13,7 +13,8 @@ weights from 0 (European) to 100, positive and negative constant
 correlations, dividends, maturities, strikes and rates, and ragged sizes
 (n just above 2 p, M and N from 1).  Tolerances are those of the fixed
 cases: 1e-9 of the integrand's scale in FP64, MIXED_C_TOL of it in mixed
-precision, and 1e-9 relative on the FP64 coefficients alpha^{k+1}.
+precision, and 1e-9 relative on the FP64 coefficients alpha^{k+1}.  Whole
+FP64 solves on random small configurations close the file.
 """
 import random
 
@@ -73,3 +74,47 @@ def test_random_configuration(k, prec):
     assert np.max(np.abs(c - it["c"])) < tol * sc, (cfg["d"], cfg["eta"], cfg["vol"]["kind"], ev)
     if prec == "fp64":
         assert rel(a1, it["alpha"]) < 1e-9
+
+
+# Whole FP64 solves (several Picard iterations, points redrawn each time,
+# refit and update on the device, with and without the captured graph)
+# against the oracle's own solve, on seeded random small configurations.
+# The penalty weight stays <= 1 (with maturities <= 2): there the Picard map
+# contracts, so the rounding differences of the two sides (libm ulps,
+# summation order) are not amplified past 1e-9 over the iterations.
+N_SOLVES = 8
+
+
+def _random_solve_case(k):
+    rng = random.Random(9100 + k)
+    d = rng.randint(1, 6)
+    eta = rng.randint(1, 4 if d <= 3 else 3)
+    p = workloads.basis_size(d, eta)
+    kind = rng.choice(["const", "abs_tanh", "sin_tanh"])
+    if kind == "const":
+        vol = {"kind": "const", "a": [rng.uniform(0.1, 0.3) for _ in range(d)]}
+    else:
+        vol = {"kind": kind, "a": rng.uniform(0.12, 0.25), "b": rng.uniform(0.02, 0.1),
+               "kappa": float(np.log(100.0))}
+    cfg = workloads.make(d=d, T=rng.choice([0.5, 1.0, 2.0]), r=rng.uniform(0.0, 0.05),
+                         K=rng.uniform(85.0, 115.0), S0=100.0, vol=vol,
+                         rho=0.0 if d == 1 else rng.choice([0.0, 0.3]),
+                         lam=rng.choice([0.0, 0.5, 1.0]), n=2 * p + rng.randint(5, 60),
+                         M=rng.randint(8, 60), N=rng.randint(2, 8), eta=eta,
+                         K_it=rng.randint(2, 3), seed=rng.randint(1, 10**6),
+                         payoff=rng.choice(["put", "call"]))
+    return cfg, rng.choice([0, 1])
+
+
+@pytest.mark.parametrize("k", range(N_SOLVES))
+def test_random_fp64_solve(k):
+    import paper_1102_4666_gb300 as G
+    cfg, use_graph = _random_solve_case(k)
+    s = G.Solver(cfg, precision="fp64")
+    rep = s.solve(use_graph=use_graph)
+    alpha = s.coeffs()
+    s.close()
+    assert rep.status == G.OK
+    ref = O.solve(cfg, nthreads=NTH)
+    assert rel(alpha, ref["alpha"]) < 1e-9
+    assert abs(rep.price - ref["price"]) <= 1e-9 * max(abs(ref["price"]), 1e-3)
