@@ -14,7 +14,8 @@ correlations, dividends, maturities, strikes and rates, and ragged sizes
 (n just above 2 p, M and N from 1).  Tolerances are those of the fixed
 cases: 1e-9 of the integrand's scale in FP64, MIXED_C_TOL of it in mixed
 precision, and 1e-9 relative on the FP64 coefficients alpha^{k+1}.  Whole
-FP64 solves on random small configurations close the file.
+FP64 solves on random small configurations against the oracle's solve, and
+whole mixed solves against FP64 ones, close the file.
 """
 import random
 
@@ -118,3 +119,45 @@ def test_random_fp64_solve(k):
     ref = O.solve(cfg, nthreads=NTH)
     assert rel(alpha, ref["alpha"]) < 1e-9
     assert abs(rep.price - ref["price"]) <= 1e-9 * max(abs(ref["price"]), 1e-3)
+
+
+# Whole mixed-precision solves against whole FP64 solves of the same random
+# numbers (the FP64 path being pinned to the oracle above): the price and
+# the deltas at (0, x0) within 1e-4 relative, on seeded random
+# configurations of every dimension and evaluation form.
+N_MIXED = 8
+
+
+def _random_mixed_case(k):
+    rng = random.Random(9300 + k)
+    d = rng.randint(1, 10)
+    eta = rng.randint(2, 6 if d <= 2 else (4 if d <= 5 else 3))
+    p = workloads.basis_size(d, eta)
+    kind = rng.choice(["const", "abs_tanh", "sin_tanh"])
+    if kind == "const":
+        vol = {"kind": "const", "a": [rng.uniform(0.1, 0.3) for _ in range(d)]}
+    else:
+        vol = {"kind": kind, "a": rng.uniform(0.12, 0.25), "b": rng.uniform(0.02, 0.1),
+               "kappa": float(np.log(100.0))}
+    return workloads.make(d=d, T=rng.choice([0.5, 1.0]), r=rng.uniform(0.0, 0.05),
+                          K=rng.uniform(90.0, 110.0), S0=100.0, vol=vol,
+                          rho=0.0 if d == 1 else rng.choice([0.0, 0.3]),
+                          lam=rng.choice([0.0, 1.0]), n=2 * p + rng.randint(50, 300),
+                          M=rng.randint(200, 600), N=rng.randint(8, 30), eta=eta, K_it=3,
+                          seed=rng.randint(1, 10**6), payoff=rng.choice(["put", "call"]))
+
+
+@pytest.mark.parametrize("k", range(N_MIXED))
+def test_random_mixed_solve_against_fp64(k):
+    import paper_1102_4666_gb300 as G
+    cfg = _random_mixed_case(k)
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = G.Solver(cfg, precision=prec)
+        r = s.solve(use_graph=1)
+        s.close()
+        assert r.status == G.OK
+        out[prec] = (r.price, np.array(r.delta[:cfg["d"]]))
+    (pm, dm), (pf, df) = out["mixed"], out["fp64"]
+    assert abs(pm - pf) <= 1e-4 * abs(pf)
+    assert np.max(np.abs(dm - df)) <= 1e-4 * max(np.max(np.abs(df)), 1e-3)
