@@ -1176,15 +1176,16 @@ __device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
 // The path kernel.  FP32 paths with the dense degree-3 and degree-4
 // evaluations run with at most 96 registers per thread at d >= 8 (five
 // 128-thread CTAs per SM, a few values spilled outside the step loop) and 80
-// below (six), the prefix-tree evaluations at d <= 5 with at most 80 (three
+// below (six), the prefix-tree evaluations at d <= 6 with at most 80 (three
 // 256-thread CTAs); FP64 paths, the Chebyshev tables and the prefix-tree
-// evaluations at d >= 6 (whose 256-thread CTAs share the instruction fetches
-// of their long straight-line evaluation, and which would spill hundreds of
-// bytes under a cap) at two 256-thread CTAs with up to 128.  Measured per
+// evaluations at d >= 7 (whose 256-thread CTAs share the instruction fetches
+// of their long straight-line evaluation, and which spill hundreds of bytes
+// under a cap: d = 10 degree 4 4.67 -> 4.84 ms with 96 registers, d = 8
+// even) at two 256-thread CTAs with up to 128.  Measured per
 // launch at the best shape: d = 10 degree 3 17.41 -> 17.18 ms (80 registers:
 // 17.40), d = 5 degree 4 3.51 -> 3.41 ms, d = 6 degree 3 0.911 -> 0.896 ms
 // (96 registers: 0.914), d = 5 degree 6 4.79 -> 4.64 ms, d = 2 degree 6
-// 1.22 -> 1.18 ms (64 registers: slower).
+// 1.22 -> 1.18 ms (64 registers: slower), d = 6 degree 4 1.62 -> 1.57 ms.
 template <int VK, int EV, bool CC, typename R, int D>
 __global__ void __launch_bounds__(256, 2) k_paths(const __grid_constant__ Args<R, D> a) {
   paths_cta<VK, EV, CC, R, D>(a);
@@ -1195,7 +1196,7 @@ __global__ void __maxnreg__(D >= 8 ? 96 : 80) k_paths_lr(const __grid_constant__
 }
 template <int EV, typename R, int D>
 constexpr bool paths_lr() {
-  return sizeof(R) == 4 && (EV == EV_DENSE3 || EV == EV_DENSE4 || (EV >= EV_TREE4 && D <= 5));
+  return sizeof(R) == 4 && (EV == EV_DENSE3 || EV == EV_DENSE4 || (EV >= EV_TREE4 && D <= 6));
 }
 
 // dynamic shared memory of the path kernel; dense: p is the number of
