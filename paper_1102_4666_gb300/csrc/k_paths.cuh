@@ -306,40 +306,59 @@ __device__ __forceinline__ void term(const R* __restrict__ tb, int S, int eta, i
 // triangle selected by a test on the indices: the trip counts are then
 // compile-time constants at every nesting level, so the loops unroll
 // completely and the vectors z, zT, bt and st stay in registers.
-template <typename R, int D>
+// CS = 2 (FP32 paths only): every coefficient is stored twice, and the four
+// accumulations of the innermost level, (av, aT) += t (z_k, zT_k) and
+// (ab, as) += t (bt_k, st_k), run as two packed FP32x2 multiply-adds on a
+// (t, t) load -- the same IEEE operations (st_0 = 0 adds an exact zero).
+template <typename R, int D, int CS = 1>
 __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __restrict__ beta,
                                             const R (&z)[D + 1], const R (&zT)[D + 1],
                                             const R (&bt)[D + 1], const R (&st)[D + 1], R& u,
                                             R& gen, R& uT) {
+  static_assert(CS == 1 || (CS == 2 && sizeof(R) == 4), "paired coefficients are FP32 only");
   constexpr int DP = D + 1;
   constexpr int NQ = DP * (DP + 1) / 2;
-  const R* bg = beta + 1;
-  const R* bq = bg + DP;
-  const R* bc3 = bq + NQ;
+  const R* bg = beta + CS;
+  const R* bq = bg + CS * DP;
+  const R* bc3 = bq + CS * NQ;
   // one pass over the coefficients for both points: value, d_bt, d_st,
   // d2_st and the weighted Hessian diagonal at (tau, X_tau), value at (T, X_T)
   R uv = beta[0], ub = R(0), us = R(0), uss = R(0), diag = R(0), sT = beta[0];
   int iq = 0, it = 0;
 #pragma unroll
   for (int i = 0; i < DP; ++i) {
-    R bv = bg[i], bb = R(0), bs = R(0), bss = R(0), bT = bg[i];
+    R bv = bg[CS * i], bb = R(0), bs = R(0), bss = R(0), bT = bg[CS * i];
 #pragma unroll
     for (int j = 0; j < DP; ++j) {
       if (j < i) continue;
-      const R q = bq[iq++];
+      const R q = bq[CS * iq++];
       R av = q, ab = R(0), as = R(0), aT = q;
+      float2 AVT = make_float2(q, q), ABS = make_float2(0.f, 0.f);  // CS = 2: (av, aT), (ab, as)
       if (i == j && i > 0) diag += R(2) * st[i] * st[i] * q;
 #pragma unroll
       for (int k = 0; k < DP; ++k) {
         if (k < j) continue;
-        const R t = bc3[it++];
-        av += t * z[k];
-        ab += t * bt[k];
-        if (k > 0) as += t * st[k];
-        aT += t * zT[k];
+        const R t = bc3[CS * it];
+        if constexpr (CS == 2) {
+          const float2 tt = reinterpret_cast<const float2*>(bc3)[it];
+          AVT = __ffma2_rn(tt, make_float2(z[k], zT[k]), AVT);
+          ABS = __ffma2_rn(tt, make_float2(bt[k], st[k]), ABS);
+        } else {
+          av += t * z[k];
+          ab += t * bt[k];
+          if (k > 0) as += t * st[k];
+          aT += t * zT[k];
+        }
+        ++it;
         if (i == j && j < k && i > 0) diag += R(2) * st[i] * st[i] * t * z[k];
         if (i < j && j == k && j > 0) diag += R(2) * st[j] * st[j] * t * z[i];
         if (i == j && j == k && i > 0) diag += R(6) * st[i] * st[i] * t * z[i];
+      }
+      if constexpr (CS == 2) {
+        av = AVT.x;
+        aT = AVT.y;
+        ab = ABS.x;
+        as = ABS.y;
       }
       // (z_j, bt_j, st_j, 0) * (av, ab, as, 0)
       bv += z[j] * av;
@@ -838,9 +857,9 @@ __device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
 
   // shared memory carve-up (dense evaluation: no multi-index or Chebyshev
   // tables; alpha holds the monomial coefficients, p of them)
-  // the prefix-tree and degree-4 evaluations (FP32 paths) keep every
-  // coefficient twice (eval_tree_x2, eval_dense4 with CS = 2)
-  constexpr bool PAIRS = (EV >= EV_TREE4 || EV == EV_DENSE4) && sizeof(R) == 4;
+  // the dense evaluations with FP32 paths keep every coefficient twice
+  // (eval_tree_x2, eval_dense3 and eval_dense4 with CS = 2)
+  constexpr bool PAIRS = EV != EV_TABLES && sizeof(R) == 4;
   R* tab = reinterpret_cast<R*>(smem_raw);                         // N x tab_stride
   R* s_alpha;                                                       // p (2 p with PAIRS)
   R* s_cp;                                                          // DP x DP
@@ -1107,7 +1126,7 @@ __device__ __forceinline__ void paths_cta(const Args<R, D>& a) {
       else if constexpr (EV == EV_DENSE4)
         eval_dense4<R, D, PAIRS ? 2 : 1>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
       else
-        eval_dense3<R, D>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
+        eval_dense3<R, D, PAIRS ? 2 : 1>(a, s_alpha, z, zT, bt, st, u, gsum, uT);
     } else {
       // per-thread Chebyshev tables: value, drift- and diffusion-scaled
       // derivatives at (tau, X_tau), value at (T, X_T)
@@ -1353,7 +1372,7 @@ cudaError_t launch(const ModelHost& m, const GridHost& g, const ProblemDev& P, i
       a.alpha = reinterpret_cast<const R*>(P.beta);
   }
   const size_t smem = smem_bytes(D, a.p, a.eta, N, tpb, sizeof(R), dense, a.tab_stride,
-                                dense && (P.tree > 0 || P.dense4) && sizeof(R) == 4,
+                                dense && sizeof(R) == 4,
                                 dense && copy_smem(P.tree > 0 ? EV_TREE4 : P.dense4 ? EV_DENSE4 : EV_DENSE3,
                                                    sizeof(R) == 4, D));
   const int vk = (m.vol_kind == 0)   ? VK_CONST

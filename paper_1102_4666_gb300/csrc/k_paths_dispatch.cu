@@ -17,8 +17,7 @@ size_t paths_smem_bytes(int d, int p, int eta, int N, int tpb, bool mixed, bool 
   // an upper bound for every volatility family and evaluation form: the tanh
   // families tabulate two coefficients per asset and step (rows padded to 16
   // bytes), and a dense evaluation with FP32 paths may keep its coefficients
-  // twice (the prefix-tree and degree-4 forms) and keep the states around
-  // the random time (copy_smem)
+  // twice and keep the states around the random time (copy_smem)
   return paths::smem_bytes(d, p, eta < 1 ? 1 : eta, N, tpb, mixed ? sizeof(float) : sizeof(double),
                            dense, (2 * (d < 3 ? 3 : d) + 3) & ~3, dense && mixed, dense && mixed);
 }
