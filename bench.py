@@ -37,11 +37,11 @@ FP32_LANES = 128  # FP32 lanes per SM (sm_103a)
 # (146.2 KB read, 0 B written: the partial sums stay in L2), scaled to a
 # launch over n points (the kernel reads the points and coefficients and
 # writes one partial sum per (point, chunk), both proportional to n).
-PATH_TRAFFIC_BYTES_PER_POINT = (137728.0 + 0.0) / 800.0
+PATH_TRAFFIC_BYTES_PER_POINT = (134656.0 + 0.0) / 800.0
 # instruction issue of the same capture: instructions per path-step and
 # instructions issued per SM cycle (of 4), and the MUFU (XU) pipe's share
-PATH_ISSUE = {"instructions_per_path_step": 254.7, "ipc": 2.45, "ipc_peak": 4.0, "xu_pipe_busy": 0.678,
-              "fma_heavy_pipe_busy": 0.645}
+PATH_ISSUE = {"instructions_per_path_step": 251.2, "ipc": 2.44, "ipc_peak": 4.0, "xu_pipe_busy": 0.682,
+              "fma_heavy_pipe_busy": 0.648}
 
 
 def env_rank():

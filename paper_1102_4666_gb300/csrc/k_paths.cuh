@@ -309,7 +309,9 @@ __device__ __forceinline__ void term(const R* __restrict__ tb, int S, int eta, i
 // CS = 2 (FP32 paths only): every coefficient is stored twice, and the four
 // accumulations of the innermost level, (av, aT) += t (z_k, zT_k) and
 // (ab, as) += t (bt_k, st_k), run as two packed FP32x2 multiply-adds on a
-// (t, t) load -- the same IEEE operations (st_0 = 0 adds an exact zero).
+// (t, t) load (the same IEEE operations; st_0 = 0 adds an exact zero); the
+// next level's (bv, bT) and (bb, bs) as three more (the sums of bb and bs
+// then associate as (b + bt_j av) + z_j ab).
 template <typename R, int D, int CS = 1>
 __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __restrict__ beta,
                                             const R (&z)[D + 1], const R (&zT)[D + 1],
@@ -328,6 +330,7 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
 #pragma unroll
   for (int i = 0; i < DP; ++i) {
     R bv = bg[CS * i], bb = R(0), bs = R(0), bss = R(0), bT = bg[CS * i];
+    float2 BVT = make_float2(bv, bT), BBS = make_float2(0.f, 0.f);  // CS = 2: (bv, bT), (bb, bs)
 #pragma unroll
     for (int j = 0; j < DP; ++j) {
       if (j < i) continue;
@@ -361,18 +364,32 @@ __device__ __forceinline__ void eval_dense3(const Args<R, D>& a, const R* __rest
         as = ABS.y;
       }
       // (z_j, bt_j, st_j, 0) * (av, ab, as, 0)
-      bv += z[j] * av;
-      bb += z[j] * ab + bt[j] * av;
-      if (j > 0) {
-        bs += z[j] * as + st[j] * av;
-        bss += R(2) * st[j] * as;
+      if constexpr (CS == 2) {
+        // (bv, bT) += (z_j, zT_j) (av, aT); (bb, bs) += (bt_j, st_j) av + z_j (ab, as)
+        BVT = __ffma2_rn(make_float2(z[j], zT[j]), make_float2(av, aT), BVT);
+        BBS = __ffma2_rn(make_float2(bt[j], st[j]), make_float2(av, av), BBS);
+        BBS = __ffma2_rn(make_float2(z[j], z[j]), make_float2(ab, as), BBS);
+        if (j > 0) bss += R(2) * st[j] * as;
       } else {
-        bs += z[j] * as;
+        bv += z[j] * av;
+        bb += z[j] * ab + bt[j] * av;
+        if (j > 0) {
+          bs += z[j] * as + st[j] * av;
+          bss += R(2) * st[j] * as;
+        } else {
+          bs += z[j] * as;
+        }
+        bT += zT[j] * aT;
       }
-      bT += zT[j] * aT;
       // keep the coefficient loads of one (i, j) group together: without
       // this fence the scheduler hoists all of them and runs out of registers
       asm volatile("" ::: "memory");
+    }
+    if constexpr (CS == 2) {
+      bv = BVT.x;
+      bT = BVT.y;
+      bb = BBS.x;
+      bs = BBS.y;
     }
     // (z_i, bt_i, st_i, 0) * (bv, bb, bs, bss)
     uv += z[i] * bv;
